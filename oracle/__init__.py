@@ -1,0 +1,259 @@
+"""Azimuthal-integration ORACLE -- test infrastructure, not product code.
+
+A plain, slow, double-precision CPU statement of the method of Kieffer & Ashiotis,
+"PyFAI: a Python library for high performance azimuthal integration on GPU" (EuroSciPy
+2014).  The arithmetic lives in ``azint_oracle.c`` (plain C, compiled without FMA
+contraction); this module only builds it with gcc, loads it with ctypes and converts
+NumPy arrays.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline arm of
+``bench.py`` may import it.  It shares no code with the CUDA package and never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+UNIT_2TH_DEG, UNIT_Q_NM, UNIT_R_MM = 0, 1, 2
+SPLIT_NONE, SPLIT_BBOX, SPLIT_FULL = 0, 1, 2
+UNITS = {"2th_deg": UNIT_2TH_DEG, "q_nm^-1": UNIT_Q_NM, "r_mm": UNIT_R_MM}
+SPLITS = {"none": SPLIT_NONE, "bbox": SPLIT_BBOX, "full": SPLIT_FULL}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "azint_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, no FMA contraction) into oracle/_build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Geom(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("dist", "poni1", "poni2", "rot1", "rot2", "rot3", "pixel1", "pixel2",
+                 "wavelength")]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        D = ctypes.POINTER(ctypes.c_double)
+        G = ctypes.POINTER(_Geom)
+        vp = ctypes.c_void_p
+        lib.orc_rotation.argtypes = [ctypes.c_double] * 3 + [D]
+        lib.orc_position_at.argtypes = [G, ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D]
+        for name in ("orc_corner_positions", "orc_centre_positions"):
+            getattr(lib, name).argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        lib.orc_solid_angle.argtypes = [G, ctypes.c_int, ctypes.c_int, vp]
+        lib.orc_polarization.argtypes = [G, ctypes.c_int, ctypes.c_int, ctypes.c_double, vp]
+        lib.orc_csr_build.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_csr_build.restype = vp
+        lib.orc_csr_free.argtypes = [vp]
+        lib.orc_csr_nnz.argtypes = [vp]
+        lib.orc_csr_nnz.restype = ctypes.c_int64
+        lib.orc_csr_nrows.argtypes = [vp]
+        lib.orc_csr_range.argtypes = [vp, D]
+        lib.orc_csr_copy.argtypes = [vp, vp, vp, vp]
+        lib.orc_integrate.argtypes = [ctypes.c_int] + [vp] * 12
+        lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 10
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+@dataclass(frozen=True)
+class Geometry:
+    """PONI-style detector geometry: distances and pixel sizes in metres, angles in rad."""
+    dist: float
+    poni1: float
+    poni2: float
+    rot1: float = 0.0
+    rot2: float = 0.0
+    rot3: float = 0.0
+    pixel1: float = 100e-6
+    pixel2: float = 100e-6
+    wavelength: float = 1.0e-10
+
+    def _c(self):
+        return _Geom(self.dist, self.poni1, self.poni2, self.rot1, self.rot2, self.rot3,
+                     self.pixel1, self.pixel2, self.wavelength)
+
+
+def rotation(rot1, rot2, rot3):
+    R = np.zeros(9)
+    _load().orc_rotation(rot1, rot2, rot3, R.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return R.reshape(3, 3)
+
+
+def position_at(geom: Geometry, unit: int, d1: float, d2: float):
+    r, c = ctypes.c_double(), ctypes.c_double()
+    g = geom._c()
+    _load().orc_position_at(ctypes.byref(g), unit, d1, d2, ctypes.byref(r), ctypes.byref(c))
+    return r.value, c.value
+
+
+def corner_positions(geom: Geometry, ny: int, nx: int, unit: int):
+    rad = np.empty((ny + 1, nx + 1))
+    chi = np.empty((ny + 1, nx + 1))
+    g = geom._c()
+    _load().orc_corner_positions(ctypes.byref(g), ny, nx, unit, _ptr(rad), _ptr(chi))
+    return rad, chi
+
+
+def centre_positions(geom: Geometry, ny: int, nx: int, unit: int):
+    rad = np.empty((ny, nx))
+    chi = np.empty((ny, nx))
+    g = geom._c()
+    _load().orc_centre_positions(ctypes.byref(g), ny, nx, unit, _ptr(rad), _ptr(chi))
+    return rad, chi
+
+
+def solid_angle(geom: Geometry, ny: int, nx: int):
+    out = np.empty((ny, nx))
+    g = geom._c()
+    _load().orc_solid_angle(ctypes.byref(g), ny, nx, _ptr(out))
+    return out
+
+
+def polarization(geom: Geometry, ny: int, nx: int, factor: float):
+    out = np.empty((ny, nx))
+    g = geom._c()
+    _load().orc_polarization(ctypes.byref(g), ny, nx, factor, _ptr(out))
+    return out
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__("oracle error %d" % code)
+        self.code = code
+
+
+@dataclass
+class Csr:
+    """bins x pixels weight matrix in scipy-compatible CSR form (Sec. 5.2.1)."""
+    indptr: np.ndarray   # int64 [nrows + 1]
+    indices: np.ndarray  # int32 [nnz], ascending within a row
+    data: np.ndarray     # float64 [nnz]
+    nrows: int
+    ny: int
+    nx: int
+    npt_rad: int
+    npt_azim: int
+    lo: float
+    hi: float
+    delta: float
+
+    @property
+    def nnz(self):
+        return int(self.indices.shape[0])
+
+    def scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.data, self.indices, self.indptr),
+                             shape=(self.nrows, self.ny * self.nx))
+
+
+def csr_build(ny, nx, rad, chi, mask, npt_rad, npt_azim, split) -> Csr:
+    """Build the weight matrix from positions: pixel-centre arrays (ny, nx) for split NONE,
+    corner arrays (ny+1, nx+1) otherwise.  ``chi`` may be None for 1D NONE/BBOX."""
+    lib = _load()
+    rad = _f64(rad)
+    chi = _f64(chi)
+    m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+    err = ctypes.c_int(0)
+    h = lib.orc_csr_build(ny, nx, _ptr(rad), _ptr(chi), _ptr(m), npt_rad, npt_azim, split,
+                          ctypes.byref(err))
+    if not h:
+        raise OracleError(err.value)
+    try:
+        nnz = lib.orc_csr_nnz(h)
+        nrows = lib.orc_csr_nrows(h)
+        rng = np.zeros(3)
+        lib.orc_csr_range(h, rng.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        indptr = np.empty(nrows + 1, np.int64)
+        indices = np.empty(max(nnz, 1), np.int32)
+        data = np.empty(max(nnz, 1), np.float64)
+        lib.orc_csr_copy(h, _ptr(indptr), _ptr(indices), _ptr(data))
+    finally:
+        lib.orc_csr_free(h)
+    return Csr(indptr, indices[:nnz], data[:nnz], nrows, ny, nx, npt_rad, npt_azim,
+               float(rng[0]), float(rng[1]), float(rng[2]))
+
+
+def positions_for(geom: Geometry, ny, nx, unit, split, npt_azim):
+    """The position arrays the split mode reads: (rad, chi) at centres or corners."""
+    if split == SPLIT_NONE:
+        return centre_positions(geom, ny, nx, unit)
+    return corner_positions(geom, ny, nx, unit)
+
+
+def build_from_geometry(geom: Geometry, ny, nx, unit, split, npt_rad, npt_azim=0,
+                        mask=None) -> Csr:
+    rad, chi = positions_for(geom, ny, nx, unit, split, npt_azim)
+    return csr_build(ny, nx, rad, chi, mask, npt_rad, npt_azim, split)
+
+
+def _csr_arrays(A: Csr):
+    return (np.ascontiguousarray(A.indptr, dtype=np.int64),
+            np.ascontiguousarray(A.indices, dtype=np.int32),
+            np.ascontiguousarray(A.data, dtype=np.float64))
+
+
+def integrate(A: Csr, image, dark=None, flat=None, solid_angle=None, polarization=None):
+    """(I, S, N, C) per bin in float64; inputs are promoted exactly to float64."""
+    lib = _load()
+    img = _f64(np.asarray(image).reshape(-1))
+    dark, flat, sa, pol = (None if a is None else _f64(np.asarray(a).reshape(-1))
+                           for a in (dark, flat, solid_angle, polarization))
+    I, S, N, C = (np.empty(A.nrows) for _ in range(4))
+    ip, ix, dt = _csr_arrays(A)
+    lib.orc_integrate(A.nrows, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(img), _ptr(dark), _ptr(flat),
+                      _ptr(sa), _ptr(pol), _ptr(I), _ptr(S), _ptr(N), _ptr(C))
+    return I, S, N, C
+
+
+def backward(A: Csr, grad_I, I, N, solid_angle=None, polarization=None):
+    """(dL/dimage, dL/dflat) per pixel in float64 for upstream gradient dL/dI."""
+    lib = _load()
+    g, I, N = (_f64(np.asarray(a).reshape(-1)) for a in (grad_I, I, N))
+    sa, pol = (None if a is None else _f64(np.asarray(a).reshape(-1))
+               for a in (solid_angle, polarization))
+    npix = A.ny * A.nx
+    gi = np.empty(npix)
+    gf = np.empty(npix)
+    ip, ix, dt = _csr_arrays(A)
+    lib.orc_backward(A.nrows, npix, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(g), _ptr(I), _ptr(N),
+                     _ptr(sa), _ptr(pol), _ptr(gi), _ptr(gf))
+    return gi, gf
+
+
+def radial_axis(A: Csr):
+    """Bin centres lo + (k + 1/2) delta of the radial axis."""
+    return A.lo + (np.arange(A.npt_rad) + 0.5) * A.delta
