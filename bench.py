@@ -1,0 +1,406 @@
+"""Benchmark: Pilatus-6M-shape 1D azimuthal integration (2527 x 2463 uint32 frames, module-gap
+mask, q in nm^-1, 1000 bins, full pixel split, dark/flat/solid-angle/polarisation), batched
+FP32-compensated forward, frames/s.
+
+A step integrates one batch of --frames frames that are already resident in HBM (the
+batch, 3.2 GB at the default 128 frames, is far larger than the 129 MB L2, so every step
+streams it from DRAM).  Alongside the device-resident number the script reports:
+  e2e          the same metric through az_integrate_batch_host (pinned host frames, copies
+               inside the timed region);
+  roofline     achieved HBM GB/s of the dominant kernel (phase-1 frames kernel), timed with
+               CUDA events on its stream during the timed region;
+  plain        the one-frame-per-launch FP64 form on the same GPU (the comparator);
+  cpu_baseline the oracle (plain C, one thread) on a bounded sample of the same workload.
+
+--impl reference times the oracle alone on the host cores (the reference arm).
+Multi-GPU (torchrun): frames are independent, so each rank integrates its own batch on its
+own GPU with no collective on the data path (weak scaling); only the timing is reduced.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Pilatus-6M-shape 1D integration frames/s & HBM GB/s vs plain, <=1e-5 rel err"
+UNIT = "frames/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=128, help="frames per step (per GPU)")
+    ap.add_argument("--e2e-frames", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_inputs(w, og_positions):
+    """Seeded synthetic inputs of the Pilatus workload shaped on centre q values."""
+    from paper_1412_6367_gb300 import synth
+    crad = og_positions
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    dark, flat = synth.dark_flat(w.ny, w.nx, w.seed)
+    return crad, mask, dark, flat
+
+
+def algorithmic_bytes(nnz, n_unmasked, nrows, frames, dark=True):
+    """Bytes the batched integration must move: the matrix once (8 B per entry: index +
+    weight), the dark once, each frame's unmasked pixels (4 B) and 16 B of output per bin
+    and frame; the frame-independent corrections and sums are counted separately."""
+    return nnz * 8 + (n_unmasked * 4 if dark else 0) + frames * (n_unmasked * 4 + 16 * nrows)
+
+
+def phase1_frames_bytes(nnz, n_unmasked, frames):
+    """Algorithmic bytes of one phase-1 frames launch covering `frames` frames."""
+    return nnz * 8 + n_unmasked * 4 + frames * n_unmasked * 4
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the phase-1 frames kernel from the committed ncu summary,
+    if that summary was taken on the current source of the kernel."""
+    path = os.path.join(ROOT, "profiles", "phase1_frames_pilatus6m.txt")
+    src = os.path.join(ROOT, "paper_1412_6367_gb300", "csrc", "integrate.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != sha:
+        return None
+    return float(t.group(1))
+
+
+def cpu_baseline(w, seconds, rank=0):
+    """The oracle, as it stands, on a bounded sample of the workload: frames integrated one
+    after the other on one host core for about `seconds` (matrix built beforehand, untimed)."""
+    import oracle as O
+    from paper_1412_6367_gb300 import synth
+    og = O.Geometry(*w.geometry.astuple())
+    rad, chi = O.corner_positions(og, w.ny, w.nx, w.unit)
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    A = O.csr_build(w.ny, w.nx, rad, chi, mask, w.npt_rad, 0, w.split)
+    crad, _ = O.centre_positions(og, w.ny, w.nx, w.unit)
+    dark, flat = synth.dark_flat(w.ny, w.nx, w.seed)
+    sa = O.solid_angle(og, w.ny, w.nx).astype(np.float32)
+    pol = O.polarization(og, w.ny, w.nx, 0.99).astype(np.float32)
+    frames = [synth.ring_image(crad, seed=1000 + k) for k in range(4)]
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        O.integrate(A, frames[n % 4], dark, flat, sa, pol)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d Pilatus-6M frames integrated one by one by the C oracle (FP64, full "
+                      "split, corrections) in %.1f s; matrix built beforehand" % (n, el)}, A
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1412_6367_gb300 import synth
+    w = synth.pilatus_workload()
+    per_step = max(1.0, args.cpu_seconds / max(args.steps, 1))
+    import oracle as O
+    og = O.Geometry(*w.geometry.astuple())
+    rad, chi = O.corner_positions(og, w.ny, w.nx, w.unit)
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    A = O.csr_build(w.ny, w.nx, rad, chi, mask, w.npt_rad, 0, w.split)
+    crad, _ = O.centre_positions(og, w.ny, w.nx, w.unit)
+    dark, flat = synth.dark_flat(w.ny, w.nx, w.seed)
+    sa = O.solid_angle(og, w.ny, w.nx).astype(np.float32)
+    pol = O.polarization(og, w.ny, w.nx, 0.99).astype(np.float32)
+    frames = [synth.ring_image(crad, seed=1000 + k) for k in range(4)]
+
+    def step():
+        n, t0 = 0, time.perf_counter()
+        while True:
+            O.integrate(A, frames[n % 4], dark, flat, sa, pol)
+            n += 1
+            if time.perf_counter() - t0 >= per_step:
+                return n
+
+    for _ in range(args.warmup):
+        step()
+    total_frames = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        total_frames += step()
+    el = time.perf_counter() - t0
+    v = total_frames / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(w, total_frames // max(args.steps, 1)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d frames over %d steps of ~%.1f s" % (total_frames, args.steps, per_step)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_dict(w, frames):
+    return {"workload": "%s: %dx%d uint32, module-gap mask, q nm^-1, %d bins, full split, "
+                        "dark/flat/solid-angle/polarisation" % (w.name, w.ny, w.nx, w.npt_rad),
+            "frames_per_step": frames, "precision": "fp32-compensated (Kahan)",
+            "l2": "inputs larger than L2 (frame batch streamed from HBM every step)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1412_6367_gb300 import api, synth
+    w = synth.pilatus_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    t_build = time.perf_counter()
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "full", mask=mask, device=dev)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    tuned = None
+    if args.autotune:
+        tuned = ig.autotune(32)
+    info = ig.refresh_info()
+    crad, _ = g.positions(w.ny, w.nx, "q_nm^-1", "centres", chi=False, device=dev)
+    crad = crad.cpu().numpy()
+    dark, flat = synth.dark_flat(w.ny, w.nx, w.seed)
+    dark_d = torch.from_numpy(dark).to(dev)
+    flat_d = torch.from_numpy(flat).to(dev)
+    sa_d = g.solid_angle(w.ny, w.nx, device=dev)
+    pol_d = g.polarization(w.ny, w.nx, w.polarization_factor, device=dev)
+    B = args.frames
+    base = np.stack([synth.ring_image(crad, seed=1000 * rank + k) for k in range(8)])
+    frames_i32 = torch.empty((B, w.ny, w.nx), dtype=torch.int32, device=dev)
+    fb = torch.from_numpy(base.view(np.int32)).to(dev)
+    for k in range(B):
+        frames_i32[k].copy_(fb[k % 8])
+    del fb
+    frames = frames_i32.view(torch.uint32)  # the counts are uint32; moved as int32 bits
+    out = api.Result(torch.empty((B, ig.nrows), device=dev), torch.empty((B, ig.nrows), device=dev),
+                     torch.empty(ig.nrows, device=dev), torch.empty(ig.nrows, device=dev))
+
+    def step():
+        ig.integrate_batch(frames, dark_d, flat_d, sa_d, pol_d, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # parity spot check at full size against the oracle (the first frame)
+    parity = None
+    if rank == 0:
+        import oracle as O
+        og = O.Geometry(*w.geometry.astuple())
+        rad, chi = O.corner_positions(og, w.ny, w.nx, w.unit)
+        A = O.csr_build(w.ny, w.nx, rad, chi, mask, w.npt_rad, 0, w.split)
+        ref = O.integrate(A, base[0], dark, flat, sa_d.cpu().numpy(), pol_d.cpu().numpy())
+        got = out.I[0].cpu().numpy().astype(np.float64)
+        sel = np.abs(ref[0]) > 1e-3 * np.abs(ref[0]).max()
+        parity = {"max_rel_err_I": float(np.max(np.abs(got[sel] - ref[0][sel]) / np.abs(ref[0][sel]))),
+                  "nnz_oracle": int(A.nnz), "nnz_gpu": int(info["nnz"])}
+
+    # timed region (device-resident inputs)
+    clocks = Clocks(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ig.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ig.profile_enable(False)
+    clk = clocks.stop()
+    prof = ig.profile_read()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * B * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (phase-1 frames): algorithmic bytes / mean duration
+    peak, peak_kind = measured_peak()
+    n_launch, tot_ms = prof["phase1_frames"]
+    launches_per_step = sum(v[0] for v in prof.values()) / args.steps
+    chunk = min(B, 64)
+    per_launch_frames = B * args.steps / max(n_launch, 1)
+    ab = phase1_frames_bytes(info["nnz"], info["n_unmasked"], per_launch_frames)
+    achieved = ab / (tot_ms / max(n_launch, 1) / 1e3) / 1e9 if n_launch else None
+    traffic_full = ncu_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (traffic_full * per_launch_frames / 64.0) if traffic_full else None,
+                "kernel": "phase1_kernel<float,float,MODE_FRAMES,%d,U32>" % info["frames_per_pass"],
+                "algorithmic_bytes_per_launch": ab, "peak_source": peak_kind + " hbm_gbs",
+                "kernel_share_of_step": tot_ms / ms if ms else None}
+    step_bytes = algorithmic_bytes(info["nnz"], info["n_unmasked"], ig.nrows, B) + 3 * 4 * info["n_unmasked"]
+
+    # plain comparator: one frame per launch, FP64 accumulation, everything re-read
+    plain = None
+    if rank == 0:
+        f0 = frames[0]
+        for _ in range(3):
+            ig.integrate(f0, dark_d, flat_d, sa_d, pol_d, precision="fp64")
+        torch.cuda.synchronize()
+        n_plain = 50
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(n_plain):
+            ig.integrate(frames[k % B], dark_d, flat_d, sa_d, pol_d, precision="fp64")
+        b.record()
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / n_plain
+        plain = {"value": 1e3 / pms, "unit": UNIT, "ms_per_frame": pms, "precision": "fp64",
+                 "speedup_batched_fp32_vs_plain": value / world / (1e3 / pms)}
+
+    # end to end through the host-buffer API (pinned frames, copies inside the timed region)
+    e2e = None
+    if rank == 0 or world > 1:
+        Be = min(args.e2e_frames, B)
+        host = torch.from_numpy(np.stack([base[k % 8] for k in range(Be)]).view(np.int32))
+        host = host.pin_memory().view(torch.uint32)
+        oI = torch.empty((Be, ig.nrows), dtype=torch.float32).pin_memory()
+        oS = torch.empty((Be, ig.nrows), dtype=torch.float32).pin_memory()
+        ig.integrate_batch_host(host, dark_d, flat_d, sa_d, pol_d, out_I=oI, out_S=oS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ksteps = max(2, min(args.steps, 5))
+        for _ in range(ksteps):
+            ig.integrate_batch_host(host, dark_d, flat_d, sa_d, pol_d, out_I=oI, out_S=oS)
+        el = time.perf_counter() - t0
+        e2e = {"value": Be * ksteps / el * world, "unit": UNIT,
+               "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(2 * oI.numel() * 4),
+               "frames_per_step": Be, "api": "az_integrate_batch_host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(w, B), "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+                "gpix_per_s": value * w.ny * w.nx / 1e9,
+                "step_algorithmic_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
+                "plain_fp64_one_frame_per_launch": plain, "parity": parity,
+                "setup": {"csr_build_s": t_build, "nnz": info["nnz"], "n_unmasked": info["n_unmasked"],
+                          "segments": info["n_segments"], "tile": [info["tile_h"], info["tile_w"]],
+                          "rows_per_warp": info["rows_per_warp"],
+                          "frames_per_pass": info["frames_per_pass"], "autotune_ms_per_frame": tuned},
+                "kernel_ms": {k: v for k, v in prof.items()}}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,269 @@
+// Internal declarations shared by the CUDA translation units of the azint library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "azint.h"
+
+namespace azint {
+
+// ------------------------------------------------------------------------------------
+// errors
+// ------------------------------------------------------------------------------------
+int fail(int code, const char *fmt, ...);
+void clear_error();
+
+#define AZ_CUDA(expr)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return ::azint::fail(e_ == cudaErrorMemoryAllocation ? AZ_ENOMEM : AZ_ECUDA,  \
+                                 "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                                 __FILE__, __LINE__);                                      \
+    } while (0)
+
+#define AZ_TRY(expr)                                                                       \
+    do {                                                                                   \
+        int rc_ = (expr);                                                                  \
+        if (rc_ != AZ_OK) return rc_;                                                      \
+    } while (0)
+
+// Device allocation owned by the library (freed in the destructor).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(AZ_ENOMEM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return AZ_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// ------------------------------------------------------------------------------------
+// host-side objects
+// ------------------------------------------------------------------------------------
+struct GeomParams {
+    double R[9];   // laboratory rotation Rz(rot3) Ry(rot2) Rx(rot1), row-major
+    double dist, poni1, poni2, pixel1, pixel2, wavelength;
+};
+
+// Pixel-tiled layout of the matrix used by the forward kernels.  Entries are grouped by
+// (tile, row, pixel); a "segment" is the run of one matrix row inside one tile.  Each
+// tile's entries start on a multiple of 8 entries so that they can be bulk-copied.
+struct TiledLayout {
+    int th = 0, tw = 0, srow = 0;      // tile rows/cols, shared-memory row stride (words)
+    int ntx = 0, nty = 0, ntiles = 0;  // tile grid
+    int n_active = 0;                  // tiles with at least one entry
+    int nseg = 0;
+    int max_tile_entries = 0;          // padded entry count of the largest tile
+    int max_tile_segments = 0;
+    int64_t padded_nnz = 0;
+    DevBuf tile_seg_ptr;    // int32 [ntiles + 1]
+    DevBuf tile_ent_ptr;    // int32 [ntiles + 1]  (padded start of each tile's entries)
+    DevBuf active_tiles;    // int32 [n_active]
+    DevBuf seg_ent_ptr;     // int32 [nseg + 1]    (absolute, in the padded entry arrays)
+    DevBuf seg_slot;        // int32 [nseg]        (position of the segment in row order)
+    DevBuf row_slot_ptr;    // int32 [nrows + 1]
+    DevBuf ent_loc;         // uint16 [padded_nnz] (shared-memory word offset in the tile)
+    DevBuf ent_w32;         // float  [padded_nnz]
+    DevBuf ent_w64;         // double [padded_nnz]
+};
+
+}  // namespace azint
+
+struct az_geometry {
+    azint::GeomParams g;
+    double rot1, rot2, rot3;
+};
+
+namespace azint {
+// CUDA-event kernel timing (az_profile_enable / az_profile_read).
+struct Profiler {
+    bool on = false;
+    struct Rec { int kind; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~Profiler() {
+        for (auto &r : recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+}  // namespace azint
+
+struct az_integrator {
+    int device = 0;
+    int ny = 0, nx = 0, npt_rad = 0, npt_azim = 0, nrows = 0, unit = 0, split = 0;
+    int n_unmasked = 0;
+    int64_t nnz = 0;
+    double lo = 0, hi = 0, delta = 0;
+    // canonical CSR (rows = bins)
+    azint::DevBuf csr_ptr, csr_idx, csr_w64;
+    // pixel-major CSC (columns = pixels) for the adjoint
+    azint::DevBuf csc_ptr, csc_row, csc_w64, csc_w32;
+    azint::TiledLayout tl;
+    // tuning
+    int rows_per_warp = 1, frames_per_pass = 4;
+    // scratch: per-segment partial sums and per-row frame-independent sums
+    azint::DevBuf partial;     // float or double [planes][nseg]
+    size_t partial_bytes = 0;
+    azint::DevBuf norm;        // [2][nrows] (N, C) in the batch accumulation type
+    azint::DevBuf adj;         // [2][nrows] doubles: adjoint row factors g/N and g I/N
+    azint::DevBuf status;      // int32 device status word
+    // host copies for the end-to-end path
+    azint::DevBuf host_stage;  // device frames buffer for az_integrate_batch_host
+    cudaStream_t last_stream = nullptr;
+    mutable azint::Profiler prof;
+};
+
+namespace azint {
+
+// ------------------------------------------------------------------------------------
+// launch helpers implemented in the .cu files
+// ------------------------------------------------------------------------------------
+int num_sms();
+int launch_positions(const GeomParams &g, int ny, int nx, int unit, int where, double *rad,
+                     double *chi, cudaStream_t s);
+int build_integrator(int ny, int nx, const double *rad, const double *chi, int npt_rad,
+                     int npt_azim, int unit, int split, const uint8_t *mask, cudaStream_t s,
+                     az_integrator *h);
+int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s);
+
+// scan / sort primitives (csr_build.cu)
+int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+int exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+int stable_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int key_bits, cudaStream_t s);
+
+// forward / backward launchers (integrate.cu, backward.cu)
+int forward_single(const az_integrator *h, const void *image, int dtype, const float *dark,
+                   const float *flat, const float *sa, const float *pol, int precision,
+                   void *oI, void *oS, void *oN, void *oC, cudaStream_t s);
+int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
+                  const float *flat, const float *sa, const float *pol, float *oI, float *oS,
+                  float *oN, float *oC, cudaStream_t s);
+int backward(const az_integrator *h, const void *g, const void *I, const void *N, const float *sa,
+             const float *pol, int precision, void *g_img, void *g_flat, cudaStream_t s);
+int batch_norm(az_integrator *h, const float *flat, const float *sa, const float *pol, float *oN,
+               float *oC, cudaStream_t s);
+int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
+                 float *oI, float *oS, int frame_out0, cudaStream_t s);
+int max_smem_per_block();
+
+// ------------------------------------------------------------------------------------
+// device helpers
+// ------------------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint32_t max_iter = (1u << 24)) {
+    for (uint32_t it = 0; it < max_iter; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Bulk (non-tensor) TMA copy global -> shared; 16-byte aligned addresses, size % 16 == 0.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Kahan-compensated FP32 accumulation (Sec. 5.2.2): the running sum s and the compensation
+// c (value = s - c).  The product is fused into the first subtraction (one rounding).
+struct Kahan {
+    float s, c;
+};
+__device__ __forceinline__ void kahan_add(Kahan &k, float w, float v) {
+    float y = __fmaf_rn(w, v, -k.c);
+    float t = __fadd_rn(k.s, y);
+    k.c = __fsub_rn(__fsub_rn(t, k.s), y);
+    k.s = t;
+}
+// Merge b into a with an error-free TwoSum of the running sums.
+__device__ __forceinline__ void kahan_merge(Kahan &a, const Kahan &b) {
+    float t = __fadd_rn(a.s, b.s);
+    float z = __fsub_rn(t, a.s);
+    float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(b.s, z));
+    a.c = __fsub_rn(__fadd_rn(a.c, b.c), e);
+    a.s = t;
+}
+__device__ __forceinline__ float kahan_value(const Kahan &k) { return __fsub_rn(k.s, k.c); }
+
+__device__ __forceinline__ Kahan shfl_xor(const Kahan &k, int m) {
+    Kahan r;
+    r.s = __shfl_xor_sync(0xffffffffu, k.s, m);
+    r.c = __shfl_xor_sync(0xffffffffu, k.c, m);
+    return r;
+}
+#endif
+
+}  // namespace azint

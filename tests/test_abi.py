@@ -1,0 +1,55 @@
+"""The C ABI library builds, loads without a GPU and exports every function the header
+declares; host-only calls behave (CPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "azint.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(az_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1412_6367_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("az_geometry_create", "az_csr_build", "az_integrate1d", "az_integrate2d",
+                 "az_integrate_backward", "az_integrate_batch", "az_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_covers_the_header():
+    from paper_1412_6367_gb300 import _lib
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_host_only_calls():
+    import oracle as O
+    from paper_1412_6367_gb300 import api
+    g = api.Geometry(0.2, 1e-3, 2e-3, 0.1, -0.2, 0.3)
+    assert np.allclose(g.rotation(), O.rotation(0.1, -0.2, 0.3), atol=1e-15, rtol=0)
+    with pytest.raises(api.AzError) as e:
+        api.Geometry(0.1, 0, 0, wavelength=0.0)
+    assert e.value.code == -1
+    from paper_1412_6367_gb300 import _lib
+    L = _lib.load()
+    assert L.az_integrate1d(None, None, 0, None, None, None, None, 1, None, None, None, None, None) == -1
+    assert b"NULL" in L.az_last_error()
