@@ -56,6 +56,7 @@ enum az_split { AZ_SPLIT_NONE = 0, AZ_SPLIT_BBOX = 1, AZ_SPLIT_FULL = 2 };
 enum az_precision { AZ_PREC_FP64 = 0, AZ_PREC_FP32_COMP = 1 };
 enum az_dtype { AZ_DTYPE_F32 = 0, AZ_DTYPE_U32 = 1, AZ_DTYPE_I32 = 2 };
 enum az_where { AZ_WHERE_CORNERS = 0, AZ_WHERE_CENTRES = 1 };
+enum az_copy_engine { AZ_COPY_TMA = 0, AZ_COPY_ASYNC = 1 };
 
 typedef struct az_geometry az_geometry;
 typedef struct az_integrator az_integrator;
@@ -71,10 +72,13 @@ typedef struct {
     int64_t nnz;               /* matrix entries */
     double lo, hi, delta;      /* radial range and bin width, in the unit */
     int32_t tile_h, tile_w;    /* pixel tile staged in shared memory by the forward */
-    int32_t rows_per_warp;     /* matrix rows reduced concurrently by one warp */
+    int32_t rows_per_warp;     /* matrix rows a warp reduces at once in the batched forward
+                                  (one lane per row and frame: 32 / frames_per_pass) */
     int32_t frames_per_pass;   /* frames sharing one pass over the matrix (batched forward) */
     int64_t n_tiles, n_segments;
     int64_t device_bytes;      /* device memory owned by the integrator */
+    int32_t copy_engine;       /* AZ_COPY_TMA or AZ_COPY_ASYNC */
+    int32_t reserved;
 } az_info;
 
 /* ---- geometry (Sec. 3) ---------------------------------------------------------------- */
@@ -266,7 +270,9 @@ void az_multi_destroy(az_multi *plan);
  */
 int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t stream, double *best_ms);
 
-/* Set the tuning by hand (0 keeps the current value).  tile_w must be a multiple of 4. */
+/* Set the tuning by hand (0 keeps the current value).  tile_w must be a multiple of 4;
+ * frames_per_pass is 1, 2, 4, 8, 16 or 32 and rows_per_warp = 32 / frames_per_pass (either
+ * may be given; both must agree). */
 int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_per_warp,
                   int frames_per_pass);
 
@@ -288,6 +294,11 @@ int az_profile_enable(az_integrator *h, int enable);
 /* Synchronise the recorded events, add up their durations per kernel kind into *out, and
  * clear the record. */
 int az_profile_read(az_integrator *h, az_profile *out);
+
+/* How the forward stages a pixel tile into shared memory: AZ_COPY_TMA issues one bulk
+ * (cp.async.bulk) copy per tile row; AZ_COPY_ASYNC issues 16-byte cp.async copies spread
+ * over a warp.  Results are identical; only speed differs. */
+int az_set_copy_engine(az_integrator *h, int engine);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
 const char *az_last_error(void);

@@ -36,7 +36,8 @@ class Info(ctypes.Structure):
                 ("tile_h", ctypes.c_int32), ("tile_w", ctypes.c_int32),
                 ("rows_per_warp", ctypes.c_int32), ("frames_per_pass", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("n_segments", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("copy_engine", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "az_autotune": ([vp, i32, vp, ctypes.POINTER(ctypes.c_double)], i32),
     "az_set_tuning": ([vp, i32, i32, i32, i32], i32),
     "az_profile_enable": ([vp, i32], i32),
+    "az_set_copy_engine": ([vp, i32], i32),
     "az_profile_read": ([vp, ctypes.POINTER(Profile)], i32),
     "az_last_error": ([], ctypes.c_char_p),
 }

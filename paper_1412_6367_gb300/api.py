@@ -306,6 +306,12 @@ class Integrator:
         self.refresh_info()
         return best.value
 
+    def set_copy_engine(self, engine):
+        """"tma" (one bulk copy per tile row) or "async" (16-byte cp.async copies)."""
+        code = {"tma": 0, "async": 1}[engine] if isinstance(engine, str) else int(engine)
+        check(self._lib.az_set_copy_engine(self._h, code))
+        self.refresh_info()
+
     def set_tuning(self, tile_h=0, tile_w=0, rows_per_warp=0, frames_per_pass=0):
         check(self._lib.az_set_tuning(self._h, tile_h, tile_w, rows_per_warp, frames_per_pass))
         self.refresh_info()

@@ -26,13 +26,6 @@ __global__ void fill_frames_kernel(uint32_t *out, int64_t n, uint32_t seed) {
     }
 }
 
-int default_rows_per_warp(const az_integrator *h) {
-    const double avg = (double)h->nnz / std::max(h->tl.nseg, 1);
-    int g = 32;
-    while (g > 1 && avg < 4.0 * g) g >>= 1;  // about four entries per lane and segment
-    return std::min(8, 32 / std::max(g, 1));
-}
-
 int alloc_scratch(az_integrator *h) {
     const size_t nseg = (size_t)std::max(h->tl.nseg, 1);
     const size_t single = 3 * nseg * sizeof(double);
@@ -45,10 +38,15 @@ int alloc_scratch(az_integrator *h) {
 }
 
 int finish_build(az_integrator *h, cudaStream_t s) {
-    const int th = 32, tw = 64;
-    AZ_TRY(build_tiled_layout(h, th, tw, s));
-    h->rows_per_warp = default_rows_per_warp(h);
-    h->frames_per_pass = 4;
+    // defaults measured on the Pilatus-6M workload; az_autotune refines them per matrix
+    int th = 16, tw = 128;
+    if (build_tiled_layout(h, th, tw, s) != AZ_OK) {  // a denser matrix: smaller tiles
+        th = 8;
+        tw = 64;
+        AZ_TRY(build_tiled_layout(h, th, tw, s));
+    }
+    h->frames_per_pass = 8;
+    h->rows_per_warp = 32 / h->frames_per_pass;
     AZ_TRY(alloc_scratch(h));
     AZ_TRY(h->status.alloc(sizeof(int)));
     AZ_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
@@ -171,11 +169,13 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
     out->tile_h = h->tl.th; out->tile_w = h->tl.tw;
     out->rows_per_warp = h->rows_per_warp; out->frames_per_pass = h->frames_per_pass;
     out->n_tiles = h->tl.ntiles; out->n_segments = h->tl.nseg;
+    out->copy_engine = h->copy_engine;
     const DevBuf *bufs[] = {&h->csr_ptr, &h->csr_idx, &h->csr_w64, &h->csc_ptr, &h->csc_row,
                             &h->csc_w64, &h->csc_w32, &h->tl.tile_seg_ptr, &h->tl.tile_ent_ptr,
                             &h->tl.active_tiles, &h->tl.seg_ent_ptr, &h->tl.seg_slot,
                             &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_w32, &h->tl.ent_w64,
-                            &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage};
+                            &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
+                            &h->tl.tile_desc, &h->tl.tile_rec};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;
@@ -433,17 +433,28 @@ extern "C" int az_profile_read(az_integrator *h, az_profile *out) {
     return rc;
 }
 
+extern "C" int az_set_copy_engine(az_integrator *h, int engine) {
+    clear_error();
+    if (!h) return fail(AZ_EINVAL, "az_set_copy_engine: NULL integrator");
+    if (engine != AZ_COPY_TMA && engine != AZ_COPY_ASYNC)
+        return fail(AZ_EINVAL, "az_set_copy_engine: bad engine %d", engine);
+    h->copy_engine = engine;
+    return AZ_OK;
+}
+
 extern "C" int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_per_warp,
                              int frames_per_pass) {
     clear_error();
     if (!h) return fail(AZ_EINVAL, "az_set_tuning: NULL integrator");
     if (tile_h < 0 || tile_w < 0 || (tile_w % 4) != 0)
         return fail(AZ_EINVAL, "az_set_tuning: tile_w must be a multiple of 4");
-    if (rows_per_warp && rows_per_warp != 1 && rows_per_warp != 2 && rows_per_warp != 4 && rows_per_warp != 8)
-        return fail(AZ_EINVAL, "az_set_tuning: rows_per_warp must be 1, 2, 4 or 8");
-    if (frames_per_pass && frames_per_pass != 1 && frames_per_pass != 2 && frames_per_pass != 4 &&
-        frames_per_pass != 8)
-        return fail(AZ_EINVAL, "az_set_tuning: frames_per_pass must be 1, 2, 4 or 8");
+    auto pow2_upto32 = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16 || v == 32; };
+    if (rows_per_warp && !pow2_upto32(rows_per_warp))
+        return fail(AZ_EINVAL, "az_set_tuning: rows_per_warp must be 1, 2, 4, 8, 16 or 32");
+    if (frames_per_pass && !pow2_upto32(frames_per_pass))
+        return fail(AZ_EINVAL, "az_set_tuning: frames_per_pass must be 1, 2, 4, 8, 16 or 32");
+    if (rows_per_warp && frames_per_pass && rows_per_warp * frames_per_pass != 32)
+        return fail(AZ_EINVAL, "az_set_tuning: rows_per_warp * frames_per_pass must be 32");
     const int th = tile_h ? tile_h : h->tl.th, tw = tile_w ? tile_w : h->tl.tw;
     if (th != h->tl.th || tw != h->tl.tw) {
         if ((int64_t)th * (tw + 8) > 65535 || th < 1 || tw < 4)
@@ -453,8 +464,9 @@ extern "C" int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_
         AZ_TRY(alloc_scratch(h));
         AZ_CUDA(cudaDeviceSynchronize());
     }
-    if (rows_per_warp) h->rows_per_warp = rows_per_warp;
+    if (rows_per_warp) h->frames_per_pass = 32 / rows_per_warp;
     if (frames_per_pass) h->frames_per_pass = frames_per_pass;
+    h->rows_per_warp = 32 / h->frames_per_pass;
     return AZ_OK;
 }
 
@@ -477,20 +489,20 @@ extern "C" int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t str
     cudaEvent_t e0, e1;
     AZ_CUDA(cudaEventCreate(&e0));
     AZ_CUDA(cudaEventCreate(&e1));
-    const int tiles[][2] = {{32, 64}, {64, 64}, {16, 128}, {32, 32}, {16, 64}};
-    const int rpws[] = {1, 2, 4, 8};
-    const int fpps[] = {2, 4, 8};
+    const int tiles[][2] = {{16, 128}, {16, 64}, {8, 256}, {8, 128}, {32, 64}, {32, 128}, {8, 64}};
+    const int fpps[] = {4, 8, 16, 32};
+    const int engines[] = {AZ_COPY_TMA, AZ_COPY_ASYNC};
     double best = 1e30;
-    int bt = 0, br = h->rows_per_warp, bf = h->frames_per_pass;
-    const int tile_count = h->npt_azim > 0 ? 5 : 4;
+    int bt = -1, bf = h->frames_per_pass, be = h->copy_engine;
+    const int tile_count = 7;
     for (int ti = 0; ti < tile_count; ++ti) {
-        if (build_tiled_layout(h, tiles[ti][0], tiles[ti][1], s) != AZ_OK) continue;
+        if (build_tiled_layout(h, tiles[ti][0], tiles[ti][1], s) != AZ_OK) { clear_error(); continue; }
         AZ_TRY(alloc_scratch(h));
         AZ_TRY(batch_norm(h, nullptr, nullptr, nullptr, nullptr, nullptr, s));
-        for (int r : rpws)
+        for (int eg : engines)
             for (int f : fpps) {
-                h->rows_per_warp = r;
                 h->frames_per_pass = f;
+                h->copy_engine = eg;
                 float best_t = 1e30f;
                 bool ok = true;
                 for (int rep = 0; rep < 3 && ok; ++rep) {
@@ -506,17 +518,19 @@ extern "C" int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t str
                 clear_error();
                 if (ok && best_t < best) {
                     best = best_t;
-                    bt = ti; br = r; bf = f;
+                    bt = ti; bf = f; be = eg;
                 }
             }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best >= 1e30) return fail(AZ_EUNSUPPORTED, "az_autotune: no configuration ran");
+    if (bt < 0) return fail(AZ_EUNSUPPORTED, "az_autotune: no configuration ran");
     AZ_TRY(build_tiled_layout(h, tiles[bt][0], tiles[bt][1], s));
     AZ_TRY(alloc_scratch(h));
-    h->rows_per_warp = br;
     h->frames_per_pass = bf;
+    h->rows_per_warp = 32 / bf;
+    h->copy_engine = be;
     AZ_CUDA(cudaStreamSynchronize(s));
     if (best_ms) *best_ms = best / n_trial_frames;
     return AZ_OK;

@@ -93,6 +93,13 @@ struct TiledLayout {
     DevBuf ent_loc;         // uint16 [padded_nnz] (shared-memory word offset in the tile)
     DevBuf ent_w32;         // float  [padded_nnz]
     DevBuf ent_w64;         // double [padded_nnz]
+    // Per active tile: a 32-byte descriptor {tile, record offset (words), record words,
+    // entry offset, padded entry count, segment count, 0, 0} and a 16-byte aligned record
+    // {tile, ns, entry offset, entry count, slot[ns], uint16 start[ns + 1]} that the forward
+    // copies into shared memory with the tile.
+    DevBuf tile_desc;       // int32 [n_active][8]
+    DevBuf tile_rec;        // int32 [sum of record words]
+    int max_rec_words = 0;
 };
 
 }  // namespace azint
@@ -134,7 +141,7 @@ struct az_integrator {
     azint::DevBuf csc_ptr, csc_row, csc_w64, csc_w32;
     azint::TiledLayout tl;
     // tuning
-    int rows_per_warp = 1, frames_per_pass = 4;
+    int rows_per_warp = 4, frames_per_pass = 8, copy_engine = AZ_COPY_ASYNC;
     // scratch: per-segment partial sums and per-row frame-independent sums
     azint::DevBuf partial;     // float or double [planes][nseg]
     size_t partial_bytes = 0;
@@ -205,6 +212,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    uint64_t st;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(smem_addr(bar)) : "memory");
+    (void)st;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {

@@ -759,6 +759,43 @@ __global__ void diff_kernel(const int32_t *ptr, int n, int32_t *out) {
         out[t] = ptr[t + 1] - ptr[t];
 }
 
+// Record size (int32 words, multiple of 4) of one active tile.
+__global__ void rec_words_kernel(const int32_t *__restrict__ active, int n_active,
+                                 const int32_t *__restrict__ tile_seg_ptr, int32_t *__restrict__ words) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_active;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int t = active[a];
+        const int ns = tile_seg_ptr[t + 1] - tile_seg_ptr[t];
+        const int w = 4 + ns + (ns + 2) / 2;  // header, slots, uint16 starts[ns + 1]
+        words[a] = (w + 3) & ~3;
+    }
+}
+
+__global__ void rec_fill_kernel(const int32_t *__restrict__ active, int n_active,
+                                const int32_t *__restrict__ tile_seg_ptr,
+                                const int32_t *__restrict__ tile_ent_ptr,
+                                const int32_t *__restrict__ seg_start, const int32_t *__restrict__ seg_end,
+                                const int32_t *__restrict__ seg_slot, const int32_t *__restrict__ rec_off,
+                                int32_t *__restrict__ rec, int32_t *__restrict__ desc) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_active;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const int t = active[a];
+        const int s0 = tile_seg_ptr[t], ns = tile_seg_ptr[t + 1] - s0;
+        const int e0 = tile_ent_ptr[t], ne = tile_ent_ptr[t + 1] - e0;
+        const int off = rec_off[a], words = rec_off[a + 1] - off;
+        int32_t *r = rec + off;
+        r[0] = t; r[1] = ns; r[2] = e0; r[3] = ne;
+        for (int i = 0; i < ns; ++i) r[4 + i] = seg_slot[s0 + i];
+        uint16_t *st = reinterpret_cast<uint16_t *>(r + 4 + ns);
+        for (int i = 0; i < ns; ++i) st[i] = (uint16_t)(seg_start[s0 + i] - e0);
+        st[ns] = (uint16_t)(seg_end[s0 + ns - 1] - e0);
+        for (int k = 4 + ns + (ns + 2) / 2; k < words; ++k) r[k] = 0;
+        int32_t *dd = desc + 8 * a;
+        dd[0] = t; dd[1] = off; dd[2] = words; dd[3] = e0;
+        dd[4] = ne; dd[5] = ns; dd[6] = 0; dd[7] = 0;
+    }
+}
+
 int bits_for(int64_t maxval) {
     int b = 1;
     while (b < 32 && ((int64_t)1 << b) <= maxval) ++b;
@@ -1027,9 +1064,38 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_CUDA(cudaMemcpyAsync(maxes, mx.p, sizeof(maxes), cudaMemcpyDeviceToHost, s));
     AZ_CUDA(cudaStreamSynchronize(s));
 
+    if (maxes[0] > 65535)
+        return fail(AZ_EUNSUPPORTED, "a %dx%d tile holds %d matrix entries (limit 65535): use smaller tiles",
+                    th, tw, maxes[0]);
+
+    // per-tile records and descriptors
+    DevBuf rwords, roff;
+    AZ_TRY(rwords.alloc(sizeof(int32_t) * std::max(n_active, 1)));
+    AZ_TRY(roff.alloc(sizeof(int32_t) * (n_active + 1)));
+    AZ_TRY(launch_gs(rec_words_kernel, n_active, s, L.active_tiles.as<int32_t>(), n_active,
+                     L.tile_seg_ptr.as<int32_t>(), rwords.as<int32_t>()));
+    AZ_TRY(exclusive_scan_i32(rwords.as<int32_t>(), roff.as<int32_t>(), n_active, s));
+    int32_t rec_total = 0;
+    AZ_CUDA(cudaMemcpyAsync(&rec_total, roff.as<int32_t>() + n_active, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    max_kernel<<<1, 1024, 0, s>>>(rwords.as<int32_t>(), n_active, mx.as<int32_t>());
+    AZ_CUDA(cudaGetLastError());
+    int32_t max_rec = 0;
+    AZ_CUDA(cudaMemcpyAsync(&max_rec, mx.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AZ_CUDA(cudaStreamSynchronize(s));
+    AZ_TRY(L.tile_rec.alloc(sizeof(int32_t) * std::max(rec_total, 4)));
+    AZ_TRY(L.tile_desc.alloc(sizeof(int32_t) * 8 * (size_t)std::max(n_active, 1)));
+    AZ_TRY(launch_gs(rec_fill_kernel, n_active, s, L.active_tiles.as<int32_t>(), n_active,
+                     L.tile_seg_ptr.as<int32_t>(), L.tile_ent_ptr.as<int32_t>(),
+                     L.seg_ent_ptr.as<int32_t>(), L.seg_ent_ptr.as<int32_t>() + nseg,
+                     L.seg_slot.as<int32_t>(), roff.as<int32_t>(), L.tile_rec.as<int32_t>(),
+                     L.tile_desc.as<int32_t>()));
+    AZ_CUDA(cudaStreamSynchronize(s));
+
     L.th = th; L.tw = tw; L.srow = T.srow; L.ntx = T.ntx; L.nty = nty; L.ntiles = ntiles;
     L.n_active = n_active; L.nseg = nseg; L.padded_nnz = padded;
     L.max_tile_entries = maxes[0]; L.max_tile_segments = maxes[1];
+    L.max_rec_words = max_rec;
     return AZ_OK;
 }
 

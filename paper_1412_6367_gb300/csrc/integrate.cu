@@ -25,9 +25,12 @@ namespace azint {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kProducers = 4;                               // producer warps per CTA
+constexpr int kConsumers = 16;                              // consumer warps per CTA
+constexpr int kThreads = 32 * (kProducers + kConsumers);
+constexpr uint32_t kFullCount = 32u * kProducers + 1u;       // arrivals completing a stage
 constexpr int kMaxPlanes = 12;
+constexpr int kMaxStages = 8;
 
 enum Mode { MODE_SINGLE = 0, MODE_NORM = 1, MODE_FRAMES = 2 };
 
@@ -53,6 +56,7 @@ struct Inst {
     int n_items;
     int stage_entries;
     int *status;
+    const int32_t *tile_desc, *tile_rec;  // per active tile: descriptor [8] and record
 };
 
 struct StageGeom {
@@ -60,101 +64,182 @@ struct StageGeom {
     uint32_t plane_region;  // bytes of the plane region
     uint32_t ent_cap;       // entry capacity (staged entries)
     uint32_t stage_bytes;   // bytes per stage (multiple of 128)
+    uint32_t rec_cap;       // bytes reserved for the tile record
+    int nstages;            // pipeline depth
 };
 
-template <int MODE, int NIMG>
-__device__ __forceinline__ int plane_list(const Inst &d, int group, const char **base, int &nimg,
-                                          int &p_dark, int &p_flat, int &p_sa, int &p_pol) {
-    int n = 0;
-    nimg = 0;
-    if (MODE == MODE_SINGLE) {
-        base[n++] = d.img;
-        nimg = 1;
-    } else if (MODE == MODE_FRAMES) {
-        const int f0 = group * d.fpi;
-        const int nf = min(d.fpi, d.n_frames - f0);
-        for (int f = 0; f < nf; ++f) base[n++] = d.img + (size_t)(f0 + f) * (size_t)d.npix * 4u;
-        nimg = nf;
-    }
-    p_dark = p_flat = p_sa = p_pol = -1;
-    if (MODE != MODE_NORM && d.dark) { p_dark = n; base[n++] = (const char *)d.dark; }
-    if (MODE != MODE_FRAMES) {
-        if (d.flat) { p_flat = n; base[n++] = (const char *)d.flat; }
-        if (d.sa) { p_sa = n; base[n++] = (const char *)d.sa; }
-        if (d.pol) { p_pol = n; base[n++] = (const char *)d.pol; }
-    }
+// Number of planes staged per item and the base address of plane `pl`: image frames
+// first, then the corrections the mode reads (dark for single/frames; flat, solid angle,
+// polarisation for single/norm), skipping absent ones.
+template <int MODE>
+__device__ __forceinline__ int plane_count(const Inst &d, int nimg) {
+    int n = nimg;
+    if (MODE != MODE_NORM && d.dark) ++n;
+    if (MODE != MODE_FRAMES) n += (d.flat != nullptr) + (d.sa != nullptr) + (d.pol != nullptr);
     return n;
 }
 
+template <int MODE>
+__device__ __forceinline__ const char *plane_base(const Inst &d, int f0, int nimg, int pl, int &kind) {
+    if (pl < nimg) { kind = 0; return d.img + (size_t)(f0 + pl) * (size_t)d.npix * 4u; }
+    int k = pl - nimg;
+    if (MODE != MODE_NORM && d.dark) { if (k == 0) { kind = 1; return (const char *)d.dark; } --k; }
+    if (MODE != MODE_FRAMES) {
+        if (d.flat) { if (k == 0) { kind = 2; return (const char *)d.flat; } --k; }
+        if (d.sa) { if (k == 0) { kind = 3; return (const char *)d.sa; } --k; }
+        if (d.pol) { if (k == 0) { kind = 4; return (const char *)d.pol; } --k; }
+    }
+    kind = -1;
+    return nullptr;
+}
+
 __device__ __forceinline__ const Inst &inst_of(const Inst &single, const Inst *multi, int n_inst,
-                                               int64_t item, int &k) {
-    if (!multi) { k = 0; return single; }
+                                               int64_t item) {
+    if (!multi) return single;
     int lo = 0, hi = n_inst;  // last instance with item_begin <= item
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (multi[mid].item_begin <= item) lo = mid; else hi = mid;
     }
-    k = lo;
     return multi[lo];
 }
 
-template <int MODE, int NIMG, class WT>
-__device__ void issue_item(const Inst &d, int64_t local, unsigned char *stage, const StageGeom &sg,
-                           uint64_t *bar) {
+struct TileDesc {
+    int t, rec_off, rec_words, e_off, ne, ns;
+};
+
+__device__ __forceinline__ TileDesc load_desc(const Inst &d, int64_t local) {
+    const int a = (int)(local / d.n_groups);
+    const int4 *p = reinterpret_cast<const int4 *>(d.tile_desc) + 2 * (size_t)a;
+    const int4 x = __ldg(p), y = __ldg(p + 1);
+    return TileDesc{x.x, x.y, x.z, x.w, y.x, y.y};
+}
+
+// Words between two staged planes: th * srow padded to 4 (mod 32), so that the same pixel of
+// consecutive planes falls in different shared-memory banks.
+__host__ __device__ __forceinline__ uint32_t plane_stride(int th, int srow) {
+    const uint32_t p = (uint32_t)th * (uint32_t)srow;
+    return p + ((4u - p) & 31u);
+}
+
+// Stage layout: [header 256 B][tile record][planes][entry locs][entry weights].
+// Header ints: 0 ns, 1 group, 2 nimg, 3..6 word offsets of dark, flat, solid angle,
+// polarisation in the plane region (-1 = absent), 7 tile, 8 entry offset, 16.. image planes.
+constexpr uint32_t kHeaderBytes = 256;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Producer warps: stage work item `local` of instance d.  Warp 0 writes the item header,
+// bulk-copies (TMA) the tile record and entries, and -- with the TMA engine -- one bulk copy
+// per tile row of every plane.  With the cp.async engine all producer warps copy the plane
+// rows in 16-byte pieces, eight lanes per row, which sustains bandwidth on short rows.
+// Every producer thread makes exactly one arrival per item (deferred until its cp.async
+// copies land), and lane 0 of warp 0 one more after publishing the header: kFullCount.
+template <int MODE, class WT, bool TMA>
+__device__ void produce(const Inst &d, int64_t local, const TileDesc &td, unsigned char *stage,
+                        const StageGeom &sg, uint64_t *bar, int *ctr, int pwarp) {
     const int lane = threadIdx.x & 31;
-    const int a = (int)(local / d.n_groups), group = (int)(local % d.n_groups);
-    const int t = d.active_tiles[a];
+    const int group = (int)(local % d.n_groups);
+    const int t = td.t;
     const int ti = t / d.ntx, tj = t - ti * d.ntx;
     const int r0 = ti * d.th, c0 = tj * d.tw;
     const int rows = min(d.th, d.ny - r0), tweff = min(d.tw, d.nx - c0);
-    const char *base[kMaxPlanes];
-    int nimg, pd, pf, ps, pp;
-    const int np = plane_list<MODE, NIMG>(d, group, base, nimg, pd, pf, ps, pp);
-    uint32_t *planes = reinterpret_cast<uint32_t *>(stage);
-    const uint32_t pw = (uint32_t)d.th * d.srow;
+    const int f0 = group * d.fpi;
+    const int nimg = MODE == MODE_SINGLE ? 1 : (MODE == MODE_FRAMES ? min(d.fpi, d.n_frames - f0) : 0);
+    const int np = plane_count<MODE>(d, nimg);
+    const uint32_t pw = plane_stride(d.th, d.srow);
+    unsigned char *rec_dst = stage + kHeaderBytes;
+    uint32_t *planes = reinterpret_cast<uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
+    unsigned char *eloc = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
+    unsigned char *ew = eloc + sg.ent_cap * 2u;
+    const uint32_t ne = (uint32_t)td.ne;
+    const bool stage_e = d.stage_entries != 0;
 
-    // bytes this lane will copy
-    uint32_t mine = 0;
-    for (int pl = 0; pl < np; ++pl)
-        for (int ly = lane; ly < rows; ly += 32) {
-            const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
-            const uintptr_t src = reinterpret_cast<uintptr_t>(base[pl]) + 4u * (uintptr_t)q;
-            const uintptr_t lo = src & ~(uintptr_t)15;
-            const uintptr_t hi = (src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15;
-            mine += (uint32_t)(hi - lo);
+    if (pwarp == 0) {
+        uint32_t mine = 0;
+        if (TMA) {
+            for (int pl = 0; pl < np; ++pl) {
+                int kind;
+                const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
+                for (int ly = lane; ly < rows; ly += 32) {
+                    const uintptr_t src = b + 4u * (uintptr_t)((int64_t)(r0 + ly) * d.nx + c0);
+                    mine += (uint32_t)(((src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15) - (src & ~(uintptr_t)15));
+                }
+            }
         }
-    const int e0 = d.tile_ent_ptr[t], e1 = d.tile_ent_ptr[t + 1];
-    const uint32_t ne = (uint32_t)(e1 - e0);
-    if (d.stage_entries && lane == 0) mine += ne * 2u + ne * (uint32_t)sizeof(WT);
-
-    fence_proxy_async_smem();
-    if (mine) asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
-                               smem_addr(bar)), "r"(mine)
-                           : "memory");
-    for (int pl = 0; pl < np; ++pl) {
-        const int dlt = (int)((reinterpret_cast<uintptr_t>(base[pl]) >> 2) & 3u);
-        for (int ly = lane; ly < rows; ly += 32) {
-            const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
-            const uintptr_t src = reinterpret_cast<uintptr_t>(base[pl]) + 4u * (uintptr_t)q;
-            const uintptr_t lo = src & ~(uintptr_t)15;
-            const uintptr_t hi = (src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15;
-            const int m0 = (int)(q & 3);
-            const int dst_off = (m0 + dlt) >= 4 ? 4 : 0;
-            uint32_t *dst = planes + (size_t)pl * pw + (size_t)ly * d.srow + dst_off;
-            bulk_g2s(dst, reinterpret_cast<const void *>(lo), (uint32_t)(hi - lo), bar);
+        if (lane == 0) {
+            mine += (uint32_t)td.rec_words * 4u;
+            if (stage_e) mine += ne * 2u + ne * (uint32_t)sizeof(WT);
+        }
+        fence_proxy_async_smem();
+        if (mine)
+            asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                         "r"(mine)
+                         : "memory");
+        if (lane == 0) {
+            bulk_g2s(rec_dst, d.tile_rec + td.rec_off, (uint32_t)td.rec_words * 4u, bar);
+            if (stage_e && ne) {
+                bulk_g2s(eloc, d.ent_loc + td.e_off, ne * 2u, bar);
+                bulk_g2s(ew, static_cast<const WT *>(d.ent_w) + td.e_off, ne * (uint32_t)sizeof(WT), bar);
+            }
+        }
+        if (TMA) {
+            for (int pl = 0; pl < np; ++pl) {
+                int kind;
+                const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
+                const int dlt = (int)((b >> 2) & 3u);
+                for (int ly = lane; ly < rows; ly += 32) {
+                    const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
+                    const uintptr_t src = b + 4u * (uintptr_t)q;
+                    const uintptr_t lo = src & ~(uintptr_t)15;
+                    const uintptr_t hi = (src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15;
+                    const int dst_off = ((int)(q & 3) + dlt) >= 4 ? 4 : 0;
+                    bulk_g2s(planes + (size_t)pl * pw + (size_t)ly * d.srow + dst_off,
+                             reinterpret_cast<const void *>(lo), (uint32_t)(hi - lo), bar);
+                }
+            }
         }
     }
-    if (d.stage_entries && lane == 0 && ne) {
-        unsigned char *eloc = stage + sg.plane_region;
-        unsigned char *ew = eloc + sg.ent_cap * 2u;
-        bulk_g2s(eloc, d.ent_loc + e0, ne * 2u, bar);
-        bulk_g2s(ew, static_cast<const WT *>(d.ent_w) + e0, ne * (uint32_t)sizeof(WT), bar);
+    if (!TMA) {
+        // eight lanes per row, four rows per warp, rows spread over the producer warps
+        const int sub = lane >> 3, l8 = lane & 7;
+        for (int pl = 0; pl < np; ++pl) {
+            int kind;
+            const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
+            const int dlt = (int)((b >> 2) & 3u);
+            for (int ly = pwarp * 4 + sub; ly < rows; ly += 4 * kProducers) {
+                const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
+                const uintptr_t src = b + 4u * (uintptr_t)q;
+                const uintptr_t lo = src & ~(uintptr_t)15;
+                const int nch = (int)((((src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15) - lo) >> 4);
+                const int dst_off = ((int)(q & 3) + dlt) >= 4 ? 4 : 0;
+                uint32_t *dst = planes + (size_t)pl * pw + (size_t)ly * d.srow + dst_off;
+                for (int c = l8; c < nch; c += 8)
+                    cp_async16(dst + 4 * c, reinterpret_cast<const void *>(lo + 16u * (uintptr_t)c));
+            }
+        }
+        cp_async_arrive(bar);  // deferred arrival when this thread's copies have landed
+    } else {
+        mbar_arrive(bar);
     }
-    __syncwarp();
-    if (lane == 0) {
-        uint64_t st;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(smem_addr(bar)) : "memory");
-        (void)st;
+    if (pwarp == 0 && lane == 0) {
+        int *h = reinterpret_cast<int *>(stage);
+        h[0] = td.ns; h[1] = group; h[2] = nimg; h[3] = h[4] = h[5] = h[6] = -1;
+        h[7] = t; h[8] = td.e_off;
+        for (int pl = 0; pl < np; ++pl) {
+            int kind;
+            const char *b = plane_base<MODE>(d, f0, nimg, pl, kind);
+            const int o = (int)(pl * pw + ((reinterpret_cast<uintptr_t>(b) >> 2) & 3u));
+            if (kind == 0) h[16 + pl] = o; else h[2 + kind] = o;
+        }
+        *ctr = 0;          // segment claim counter of this stage
+        mbar_arrive(bar);  // publishes the header and the counter
     }
 }
 
@@ -177,172 +262,249 @@ template <> struct Acc<float> {
     Kahan k;
     __device__ void zero() { k.s = 0.f; k.c = 0.f; }
     __device__ void add(float w, float v) { kahan_add(k, w, v); }
-    __device__ void merge_xor(int m) { Kahan o = shfl_xor(k, m); kahan_merge(k, o); }
+    __device__ void merge(const Acc<float> &o) { kahan_merge(k, o.k); }
+    __device__ void merge_xor(int m) {
+        // lower lane's partial sum on the left: every lane ends with lane 0's value
+        const Kahan o = shfl_xor(k, m);
+        if ((threadIdx.x & m) != 0) {
+            Kahan l = o;
+            kahan_merge(l, k);
+            k = l;
+        } else {
+            kahan_merge(k, o);
+        }
+    }
     __device__ float value() const { return kahan_value(k); }
 };
 template <> struct Acc<double> {
     double s;
     __device__ void zero() { s = 0.0; }
     __device__ void add(double w, double v) { s = __fma_rn(w, v, s); }
+    __device__ void merge(const Acc<double> &o) { s += o.s; }
     __device__ void merge_xor(int m) { s += __shfl_xor_sync(0xffffffffu, s, m); }
     __device__ double value() const { return s; }
 };
 
-template <int R, class AT, class WT, int MODE, int NIMG, int DT>
-__device__ void reduce_tile(const Inst &d, int64_t local, const unsigned char *stage,
-                            const StageGeom &sg) {
-    constexpr int G = 32 / R;
-    constexpr int NACC = MODE == MODE_SINGLE ? 3 : (MODE == MODE_NORM ? 2 : NIMG);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane / G, li = lane % G;
-    const int a = (int)(local / d.n_groups), group = (int)(local % d.n_groups);
-    const int t = d.active_tiles[a];
-    const char *base[kMaxPlanes];
-    int nimg, pd, pf, ps, pp;
-    plane_list<MODE, NIMG>(d, group, base, nimg, pd, pf, ps, pp);
-    const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage);
-    const uint32_t pw = (uint32_t)d.th * d.srow;
-    auto off = [&](int pl) -> int {
-        return pl < 0 ? 0 : (int)(pl * pw + ((reinterpret_cast<uintptr_t>(base[pl]) >> 2) & 3u));
-    };
-    int oimg[NIMG > 0 ? NIMG : 1];
-#pragma unroll
-    for (int f = 0; f < (NIMG > 0 ? NIMG : 1); ++f) oimg[f] = off(f < nimg ? f : -1);
-    const int odark = off(pd), oflat = off(pf), osa = off(ps), opol = off(pp);
-    const int tile_e0 = d.tile_ent_ptr[t];
+// What a consumer needs about its instance, loaded once per item into registers.
+struct ConsumerParams {
+    void *partial;
+    const uint16_t *ent_loc;
+    const void *ent_w;
+    int nseg, fpi, stage_entries;
+};
+
+__device__ __forceinline__ ConsumerParams consumer_params(const Inst &d) {
+    return ConsumerParams{d.partial, d.ent_loc, d.ent_w, d.nseg, d.fpi, d.stage_entries};
+}
+
+// One lane per (segment, quantity).  A warp takes 32 / Q segments at a time from the stage's
+// claim counter; the Q lanes of a segment share its (loc, weight) stream (broadcast reads)
+// and each sums one quantity over all of the segment's entries, in entry order:
+//   frames pass: quantity q = frame q of the item, value = cast(image) - dark;
+//   norm pass:   q = 0: flat * solid angle * polarisation, q = 1: 1 (the count);
+//   single pass: q = 0: cast(image) - dark, q = 1: the normalisation, q = 2: 1, q = 3 idle.
+// Every quantity of every pass is reduced by the same sequence of operations, so a flat
+// image with unit corrections gives S == N bit for bit, and a frame integrated alone or in
+// a batch gives the same bits.  No merge between lanes is needed.
+template <int Q, class AT, class WT, int MODE, int DT, bool SE>
+__device__ void consume_serial(const ConsumerParams &cp, const unsigned char *stage,
+                               const StageGeom &sg, int *ctr) {
+    constexpr int R = 32 / Q;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / Q, q = lane % Q;
+    const int *h = reinterpret_cast<const int *>(stage);
+    const int ns = h[0], group = h[1], nimg = h[2];
+    const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
+    // this lane's image plane (frames / single passes)
+    const int oimg = h[16 + (MODE == MODE_FRAMES ? q : 0)];
+    bool active;
+    if (MODE == MODE_FRAMES) active = q < nimg;
+    else if (MODE == MODE_NORM) active = true;
+    else active = q < 3;
+    const int *slots = reinterpret_cast<const int *>(stage + kHeaderBytes) + 4;
+    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
+    const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
     const uint16_t *L;
     const WT *W;
-    if (d.stage_entries) {
-        L = reinterpret_cast<const uint16_t *>(stage + sg.plane_region);
-        W = reinterpret_cast<const WT *>(stage + sg.plane_region + sg.ent_cap * 2u);
+    if constexpr (SE) {
+        L = reinterpret_cast<const uint16_t *>(stage + kHeaderBytes + sg.rec_cap + sg.plane_region);
+        W = reinterpret_cast<const WT *>(stage + kHeaderBytes + sg.rec_cap + sg.plane_region + sg.ent_cap * 2u);
     } else {
-        L = d.ent_loc + tile_e0;
-        W = static_cast<const WT *>(d.ent_w) + tile_e0;
+        L = cp.ent_loc + h[8];
+        W = static_cast<const WT *>(cp.ent_w) + h[8];
     }
-    const int s0 = d.tile_seg_ptr[t], ns = d.tile_seg_ptr[t + 1] - s0;
-    for (int b = 0; b < ns; b += kWarps * R) {
-        const int sl = b + warp * R + grp;
-        const bool has = sl < ns;
+    // output row of this lane's quantity in the partial buffer
+    size_t orow;
+    if (MODE == MODE_FRAMES) orow = (size_t)(group * cp.fpi + q) * cp.nseg;
+    else orow = (size_t)q * cp.nseg;
+    AT *out = static_cast<AT *>(cp.partial) + orow;
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, R);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        const int sl = b + sub;
         int e0 = 0, e1 = 0, slot = 0;
-        if (has) {
-            e0 = d.seg_start[s0 + sl] - tile_e0;
-            e1 = d.seg_end[s0 + sl] - tile_e0;
-            slot = d.seg_slot[s0 + sl];
+        if (sl < ns) {
+            e0 = starts[sl];
+            e1 = starts[sl + 1];
+            slot = slots[sl];
         }
-        Acc<AT> acc[NACC];
+        if (!active) e1 = e0;
+        // four independent sums per lane (entries e0 + 4k + j in sum j), combined in a fixed
+        // order: ((a0 + a1) + (a2 + a3))
+        Acc<AT> acc[4];
 #pragma unroll
-        for (int k = 0; k < NACC; ++k) acc[k].zero();
-#pragma unroll 4
-        for (int e = e0 + li; e < e1; e += G) {
+        for (int j = 0; j < 4; ++j) acc[j].zero();
+        auto value_of = [&](int e, AT &w, AT &x) {
             const int loc = L[e];
-            const AT w = (AT)W[e];
-            if (MODE == MODE_SINGLE) {
-                AT v, n = AT(1);
-                if (sizeof(AT) == 8) {
-                    v = (AT)img_f64<DT>(planes[oimg[0] + loc]);
-                    if (pd >= 0) v = v - (AT)__uint_as_float(planes[odark + loc]);
-                } else {
-                    v = (AT)img_f32<DT>(planes[oimg[0] + loc]);
-                    if (pd >= 0) v = __fsub_rn((float)v, __uint_as_float(planes[odark + loc]));
-                }
-                if (pf >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
-                if (ps >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
-                if (pp >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
-                acc[0].add(w, v);
-                acc[1].add(w, n);
-                acc[2].add(w, AT(1));
+            w = (AT)W[e];
+            if (MODE == MODE_FRAMES) {
+                float v = img_f32<DT>(planes[oimg + loc]);
+                if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc]));
+                x = (AT)v;
             } else if (MODE == MODE_NORM) {
                 AT n = AT(1);
-                if (pf >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
-                if (ps >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
-                if (pp >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
-                acc[0].add(w, n);
-                acc[1].add(w, AT(1));
+                if (q == 0) {
+                    if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
+                    if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
+                    if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
+                }
+                x = n;
             } else {
-                const float dk = pd >= 0 ? __uint_as_float(planes[odark + loc]) : 0.f;
-#pragma unroll
-                for (int f = 0; f < NIMG; ++f) {
-                    if (f < nimg) {
-                        float v = img_f32<DT>(planes[oimg[f] + loc]);
-                        if (pd >= 0) v = __fsub_rn(v, dk);
-                        acc[f].add((float)w, v);
+                if (q == 0) {
+                    if (sizeof(AT) == 8) {
+                        x = (AT)img_f64<DT>(planes[oimg + loc]);
+                        if (odark >= 0) x = x - (AT)__uint_as_float(planes[odark + loc]);
+                    } else {
+                        float v = img_f32<DT>(planes[oimg + loc]);
+                        if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc]));
+                        x = (AT)v;
                     }
+                } else if (q == 1) {
+                    AT n = AT(1);
+                    if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
+                    if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
+                    if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
+                    x = n;
+                } else {
+                    x = AT(1);
                 }
             }
+        };
+        int e = e0;
+        for (; e + 4 <= e1; e += 4) {
+            AT w[4], x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) value_of(e + j, w[j], x[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[j].add(w[j], x[j]);
         }
 #pragma unroll
-        for (int m = G / 2; m > 0; m >>= 1)
-#pragma unroll
-            for (int k = 0; k < NACC; ++k) acc[k].merge_xor(m);
-        if (has && li == 0) {
-            AT *out = static_cast<AT *>(d.partial);
-            if (MODE == MODE_FRAMES) {
-                const int f0 = group * d.fpi;
-#pragma unroll
-                for (int f = 0; f < NACC; ++f)
-                    if (f < nimg) out[(size_t)(f0 + f) * d.nseg + slot] = acc[f].value();
-            } else {
-#pragma unroll
-                for (int k = 0; k < NACC; ++k) out[(size_t)k * d.nseg + slot] = acc[k].value();
+        for (int j = 0; j < 3; ++j) {
+            if (e + j < e1) {
+                AT w, x;
+                value_of(e + j, w, x);
+                acc[j].add(w, x);
             }
         }
+        acc[0].merge(acc[1]);
+        acc[2].merge(acc[3]);
+        acc[0].merge(acc[2]);
+        if (sl < ns && active) out[slot] = acc[0].value();
     }
 }
 
 template <class AT, class WT, int MODE, int NIMG, int DT>
-__device__ __forceinline__ void reduce_dispatch(const Inst &d, int64_t local,
-                                                const unsigned char *stage, const StageGeom &sg) {
-    switch (d.rpw) {
-        case 1: reduce_tile<1, AT, WT, MODE, NIMG, DT>(d, local, stage, sg); break;
-        case 2: reduce_tile<2, AT, WT, MODE, NIMG, DT>(d, local, stage, sg); break;
-        case 4: reduce_tile<4, AT, WT, MODE, NIMG, DT>(d, local, stage, sg); break;
-        default: reduce_tile<8, AT, WT, MODE, NIMG, DT>(d, local, stage, sg); break;
-    }
+__device__ __forceinline__ void consume_dispatch(const ConsumerParams &cp, const unsigned char *stage,
+                                                 const StageGeom &sg, int *ctr) {
+    constexpr int Q = MODE == MODE_FRAMES ? NIMG : (MODE == MODE_NORM ? 2 : 4);
+    if (cp.stage_entries) consume_serial<Q, AT, WT, MODE, DT, true>(cp, stage, sg, ctr);
+    else consume_serial<Q, AT, WT, MODE, DT, false>(cp, stage, sg, ctr);
 }
 
-template <class AT, class WT, int MODE, int NIMG, int DT>
+// Warp-specialised persistent kernel.  Warp 0 produces: for each work item of this CTA
+// (static round robin) it waits until the stage is free (empty barrier), copies the item
+// into it and arms the full barrier.  Warps 1..kConsumers consume: they wait for the item's
+// full barrier, claim and reduce its segments, and release the stage (empty barrier, one
+// arrival per consumer warp).  Every wait is bounded; a wait that gives up records
+// AZ_ETIMEOUT in the status word, raises the CTA's abort flag and leaves, the producer
+// first giving its own copies in flight a bounded grace period.
+template <class AT, class WT, int MODE, int NIMG, int DT, bool TMA>
 __global__ void __launch_bounds__(kThreads, 1)
 phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ multi, int n_inst,
               int64_t n_items, StageGeom sg) {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * (size_t)sg.stage_bytes);
-    const int warp = threadIdx.x >> 5;
+    const int S = sg.nstages;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * sg.stage_bytes);
+    uint64_t *empty = full + S;
+    int *ctr = reinterpret_cast<int *>(empty + S);
+    volatile int *abort_flag = ctr + S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int *status = single.status ? single.status : multi[0].status;
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], kFullCount);
+            mbar_init(&empty[s], kConsumers);
+        }
+        *abort_flag = 0;
         fence_barrier_init();
     }
     __syncthreads();
-    int64_t item = blockIdx.x;
-    if (item < n_items && warp == 0) {
-        int k;
-        const Inst &d = inst_of(single, multi, n_inst, item, k);
-        issue_item<MODE, NIMG, WT>(d, item - d.item_begin, smem, sg, &bars[0]);
-    }
-    for (int it = 0; item < n_items; ++it, item += gridDim.x) {
-        const int st = it & 1;
-        const int64_t next = item + gridDim.x;
-        if (next < n_items && warp == 0) {
-            int k;
-            const Inst &dn = inst_of(single, multi, n_inst, next, k);
-            issue_item<MODE, NIMG, WT>(dn, next - dn.item_begin, smem + (size_t)(st ^ 1) * sg.stage_bytes,
-                                       sg, &bars[st ^ 1]);
+    if (warp < kProducers) {
+        int k = 0;
+        int64_t item = blockIdx.x;
+        TileDesc td{};
+        if (item < n_items) {
+            const Inst &d0 = inst_of(single, multi, n_inst, item);
+            td = load_desc(d0, item - d0.item_begin);
         }
-        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((it >> 1) & 1));
-        int k;
-        const Inst &d = inst_of(single, multi, n_inst, item, k);
-        if (!__syncthreads_and(ok)) {
-            // A copy never completed: record it, give in-flight copies a bounded grace
-            // period, and leave.
-            if (threadIdx.x == 0) {
-                atomicExch(d.status, AZ_ETIMEOUT);
-                mbar_wait_bounded(&bars[st], (uint32_t)((it >> 1) & 1));
-                if (next < n_items) mbar_wait_bounded(&bars[st ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
+        for (; item < n_items; item += gridDim.x, ++k) {
+            const int s = k % S, n = k / S;
+            // prefetch the next item's descriptor while this one is staged
+            const int64_t next = item + gridDim.x;
+            TileDesc tn{};
+            if (next < n_items) {
+                const Inst &dn = inst_of(single, multi, n_inst, next);
+                tn = load_desc(dn, next - dn.item_begin);
             }
-            return;
+            bool ok = true;
+            if (n > 0) ok = mbar_wait_bounded(&empty[s], (uint32_t)((n - 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (__any_sync(0xffffffffu, !ok || *abort_flag != 0)) {  // warp-uniform decision
+                if (lane == 0) {
+                    if (!ok) atomicExch(status, AZ_ETIMEOUT);
+                    *abort_flag = 1;
+                    for (int j = k - 1; j >= 0 && j >= k - S; --j)  // grace for own copies
+                        mbar_wait_bounded(&full[j % S], (uint32_t)((j / S) & 1));
+                }
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                break;
+            }
+            const Inst &d = inst_of(single, multi, n_inst, item);
+            produce<MODE, WT, TMA>(d, item - d.item_begin, td, smem + (size_t)s * sg.stage_bytes, sg,
+                                   &full[s], &ctr[s], warp);
+            td = tn;
         }
-        reduce_dispatch<AT, WT, MODE, NIMG, DT>(d, item - d.item_begin, smem + (size_t)st * sg.stage_bytes, sg);
-        __syncthreads();
+    } else {
+        int k = 0;
+        for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
+            const int s = k % S, n = k / S;
+            bool ok = mbar_wait_bounded(&full[s], (uint32_t)(n & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (__any_sync(0xffffffffu, !ok || *abort_flag != 0)) {  // warp-uniform decision
+                if (lane == 0) {
+                    if (!ok) atomicExch(status, AZ_ETIMEOUT);
+                    *abort_flag = 1;
+                }
+                break;
+            }
+            const ConsumerParams cp = multi ? consumer_params(inst_of(single, multi, n_inst, item))
+                                            : consumer_params(single);
+            consume_dispatch<AT, WT, MODE, NIMG, DT>(cp, smem + (size_t)s * sg.stage_bytes, sg, &ctr[s]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
     }
 }
 
@@ -428,29 +590,35 @@ int g_max_smem = 0;
 
 // Stage dimensions: plane slots of `plane_words` words, `planes` of them, plus (when the
 // entries are staged) room for `ent_cap` entries of (uint16 loc, wbytes weight).
-StageGeom stage_geom(uint32_t plane_words, int planes, uint32_t ent_cap, int wbytes) {
+constexpr uint32_t kBarrierBytes = 256;  // full/empty barriers, claim counters, abort flag
+
+StageGeom stage_geom(uint32_t plane_words, int planes, uint32_t ent_cap, int wbytes, uint32_t rec_words) {
     StageGeom sg;
     sg.plane_words = plane_words;
     sg.plane_region = (uint32_t)planes * plane_words * 4u;
     sg.ent_cap = ent_cap;
-    uint32_t bytes = sg.plane_region + ent_cap * (2u + (uint32_t)wbytes);
+    sg.rec_cap = (rec_words * 4u + 15u) & ~15u;
+    uint32_t bytes = kHeaderBytes + sg.rec_cap + sg.plane_region + ent_cap * (2u + (uint32_t)wbytes);
     sg.stage_bytes = (bytes + 127u) & ~127u;
+    // as many stages as fit (at least two, at most kMaxStages)
+    const int avail = max_smem_per_block() - (int)kBarrierBytes;
+    sg.nstages = std::min(kMaxStages, std::max(2, avail / (int)sg.stage_bytes));
     return sg;
 }
 
-uint32_t smem_for(const StageGeom &sg) { return 2u * sg.stage_bytes + 64u; }
+uint32_t smem_for(const StageGeom &sg) { return (uint32_t)sg.nstages * sg.stage_bytes + kBarrierBytes; }
 
 // Stage the entries when the largest tile fits twice next to the planes; otherwise the
 // reduction reads the entries from global memory.
 StageGeom choose_stage(uint32_t plane_words, int planes, uint32_t max_entries, int wbytes,
-                       int &stage_entries) {
-    StageGeom sg = stage_geom(plane_words, planes, max_entries, wbytes);
+                       uint32_t rec_words, int &stage_entries) {
+    StageGeom sg = stage_geom(plane_words, planes, max_entries, wbytes, rec_words);
     if ((int)smem_for(sg) <= max_smem_per_block()) {
         stage_entries = 1;
         return sg;
     }
     stage_entries = 0;
-    return stage_geom(plane_words, planes, 0, wbytes);
+    return stage_geom(plane_words, planes, 0, wbytes, rec_words);
 }
 
 Inst make_inst(const az_integrator *h, bool fp64) {
@@ -466,13 +634,15 @@ Inst make_inst(const az_integrator *h, bool fp64) {
     d.ent_loc = L.ent_loc.as<uint16_t>();
     d.ent_w = fp64 ? (const void *)L.ent_w64.p : (const void *)L.ent_w32.p;
     d.ny = h->ny; d.nx = h->nx; d.th = L.th; d.tw = L.tw; d.srow = L.srow; d.ntx = L.ntx;
-    d.rpw = h->rows_per_warp; d.nseg = L.nseg; d.nrows = h->nrows;
+    d.rpw = 32 / h->frames_per_pass; d.nseg = L.nseg; d.nrows = h->nrows;
     d.npix = (int64_t)h->ny * h->nx;
     d.n_frames = 1; d.fpi = 1; d.n_groups = 1;
     d.partial = h->partial.p;
     d.norm = h->norm.as<float>();
     d.status = h->status.as<int>();
     d.n_items = L.n_active;
+    d.tile_desc = L.tile_desc.as<int32_t>();
+    d.tile_rec = L.tile_rec.as<int32_t>();
     return d;
 }
 
@@ -494,7 +664,7 @@ struct ProfScope {
     }
 };
 
-template <class AT, class WT, int MODE, int NIMG, int DT>
+template <class AT, class WT, int MODE, int NIMG, int DT, bool TMA>
 int run_phase1(const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
                const StageGeom &sg, cudaStream_t s, Profiler *prof = nullptr) {
     if (n_items <= 0) return AZ_OK;
@@ -502,7 +672,7 @@ int run_phase1(const Inst &single, const Inst *multi, int n_inst, int64_t n_item
     if ((int)smem > max_smem_per_block())
         return fail(AZ_EUNSUPPORTED, "forward: %u bytes of shared memory needed (%d available)",
                     smem, max_smem_per_block());
-    auto kern = phase1_kernel<AT, WT, MODE, NIMG, DT>;
+    auto kern = phase1_kernel<AT, WT, MODE, NIMG, DT, TMA>;
     AZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     AZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
@@ -532,20 +702,29 @@ int run_phase2(const Inst &single, const Inst *multi, int n_inst, int64_t n_jobs
     return AZ_OK;
 }
 
+template <class AT, class WT, int MODE, int NIMG, int DT>
+int run_phase1_eng(int engine, const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
+                   const StageGeom &sg, cudaStream_t s, Profiler *prof) {
+    if (engine == AZ_COPY_ASYNC)
+        return run_phase1<AT, WT, MODE, NIMG, DT, false>(single, multi, n_inst, n_items, sg, s, prof);
+    return run_phase1<AT, WT, MODE, NIMG, DT, true>(single, multi, n_inst, n_items, sg, s, prof);
+}
+
 template <class AT, class WT, int MODE, int NIMG>
-int run_phase1_dt(int dtype, const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
-                  const StageGeom &sg, cudaStream_t s, Profiler *prof = nullptr) {
+int run_phase1_dt(int dtype, int engine, const Inst &single, const Inst *multi, int n_inst,
+                  int64_t n_items, const StageGeom &sg, cudaStream_t s, Profiler *prof = nullptr) {
     switch (dtype) {
         case AZ_DTYPE_F32:
-            return run_phase1<AT, WT, MODE, NIMG, AZ_DTYPE_F32>(single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_F32>(engine, single, multi, n_inst, n_items, sg, s, prof);
         case AZ_DTYPE_U32:
-            return run_phase1<AT, WT, MODE, NIMG, AZ_DTYPE_U32>(single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_U32>(engine, single, multi, n_inst, n_items, sg, s, prof);
         default:
-            return run_phase1<AT, WT, MODE, NIMG, AZ_DTYPE_I32>(single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_I32>(engine, single, multi, n_inst, n_items, sg, s, prof);
     }
 }
 
-uint32_t plane_words_of(const az_integrator *h) { return (uint32_t)h->tl.th * h->tl.srow; }
+uint32_t plane_words_of(const az_integrator *h) { return plane_stride(h->tl.th, h->tl.srow); }
+uint32_t rec_words_of(const az_integrator *h) { return (uint32_t)h->tl.max_rec_words; }
 
 }  // namespace
 
@@ -579,12 +758,13 @@ int forward_single(const az_integrator *h, const void *image, int dtype, const f
     d.oI = oI; d.oS = oS; d.oN = oN; d.oC = oC;
     const int planes = 1 + (dark != nullptr) + (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries,
-                                fp64 ? 8 : 4, d.stage_entries);
+                                fp64 ? 8 : 4, rec_words_of(h), d.stage_entries);
+    const int eng = h->copy_engine;
     if (fp64) {
-        AZ_TRY((run_phase1_dt<double, double, MODE_SINGLE, 1>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+        AZ_TRY((run_phase1_dt<double, double, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
         AZ_TRY((run_phase2<double, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     } else {
-        AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+        AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
         AZ_TRY((run_phase2<float, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     }
     return AZ_OK;
@@ -597,34 +777,47 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
     d.oN = oN; d.oC = oC;
     const int planes = (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
-                                d.stage_entries);
-    AZ_TRY((run_phase1<float, float, MODE_NORM, 1, AZ_DTYPE_F32>(d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+                                rec_words_of(h), d.stage_entries);
+    AZ_TRY((run_phase1_eng<float, float, MODE_NORM, 1, AZ_DTYPE_F32>(h->copy_engine, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
     AZ_TRY((run_phase2<float, MODE_NORM>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     return AZ_OK;
 }
 
 int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
                  float *oI, float *oS, int frame_out0, cudaStream_t s) {
-    const int fpi = h->frames_per_pass;
+    // frames per pass as tuned, halved while two stages of that many frame planes do not fit
+    int fpi = h->frames_per_pass;
+    while (fpi > 1) {
+        int se = 0;
+        const StageGeom g = choose_stage(plane_words_of(h), fpi + (dark != nullptr),
+                                         (uint32_t)h->tl.max_tile_entries, 4, rec_words_of(h), se);
+        if ((int)smem_for(g) <= max_smem_per_block()) break;
+        fpi >>= 1;
+    }
     const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(h->tl.nseg, 1)));
     const int chunk_max = (int)std::max<int64_t>(fpi, (cap / fpi) * fpi);
     const int planes = fpi + (dark != nullptr);
     int stage_e = 0;
-    StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4, stage_e);
+    StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
+                                rec_words_of(h), stage_e);
+    const int eng = h->copy_engine;
     for (int f0 = 0; f0 < n; f0 += chunk_max) {
         const int nf = std::min(chunk_max, n - f0);
         Inst d = make_inst(h, false);
         d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
         d.n_frames = nf; d.fpi = fpi; d.n_groups = (nf + fpi - 1) / fpi;
+        d.rpw = 32 / fpi;
         d.dark = dark;
         d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
         d.stage_entries = stage_e;
         d.n_items = h->tl.n_active * d.n_groups;
         switch (fpi) {
-            case 1: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 1>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 2: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 2>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 4: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 4>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 8>(dtype, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 1: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 2: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 2>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 4: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 4>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 8: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 8>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 16: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 16>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 32>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
         }
         AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
     }
@@ -645,7 +838,7 @@ struct MultiPlan {
     std::vector<Inst> host;
     DevBuf dev;
     int n = 0;
-    int dtype = 0;
+    int dtype = 0, engine = 0;
     int64_t n_items = 0, n_rows = 0;
     StageGeom sg{};
     cudaGraphExec_t exec = nullptr;
@@ -661,7 +854,8 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
     P->n = n;
     P->dtype = dtype;
     int64_t items = 0, rows = 0;
-    uint32_t pw = 0, ecap = 0;
+    uint32_t pw = 0, ecap = 0, rw = 0;
+    P->engine = hs[0]->copy_engine;
     int planes = 0;
     for (int k = 0; k < n; ++k) {
         const az_integrator *h = hs[k];
@@ -681,12 +875,13 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
         rows += h->nrows;
         pw = std::max(pw, plane_words_of(h));
         ecap = std::max(ecap, (uint32_t)h->tl.max_tile_entries);
+        rw = std::max(rw, rec_words_of(h));
         planes = std::max(planes, 1 + (d.dark != nullptr) + (d.flat != nullptr) + (d.sa != nullptr) +
                                       (d.pol != nullptr));
         P->host.push_back(d);
     }
     int stage_e = 0;
-    P->sg = choose_stage(pw, planes, ecap, 4, stage_e);
+    P->sg = choose_stage(pw, planes, ecap, 4, rw, stage_e);
     for (auto &d : P->host) d.stage_entries = stage_e;
     P->n_items = items;
     P->n_rows = rows;
@@ -706,7 +901,7 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
 int multi_enqueue(void *plan, cudaStream_t s) {
     MultiPlan *P = static_cast<MultiPlan *>(plan);
     const Inst *dev = P->dev.as<Inst>();
-    AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(P->dtype, P->host[0], dev, P->n, P->n_items, P->sg, s)));
+    AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(P->dtype, P->engine, P->host[0], dev, P->n, P->n_items, P->sg, s)));
     AZ_TRY((run_phase2<float, MODE_SINGLE>(P->host[0], dev, P->n, P->n_rows, 1, s)));
     return AZ_OK;
 }
@@ -715,17 +910,28 @@ int multi_launch(void *plan, int use_graph, cudaStream_t s) {
     MultiPlan *P = static_cast<MultiPlan *>(plan);
     if (!use_graph) return multi_enqueue(plan, s);
     if (!P->exec) {
-        // configure the kernels once outside the capture, then capture the two launches
+        // Run once eagerly (this call's results; it also configures the kernels), then
+        // capture the two launches on a private stream: the caller's stream may be the
+        // legacy default stream, which cannot be captured.
         AZ_TRY(multi_enqueue(plan, s));
-        AZ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-        int rc = multi_enqueue(plan, s);
+        cudaStream_t cs = nullptr;
+        AZ_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        int rc = e == cudaSuccess ? multi_enqueue(plan, cs)
+                                  : fail(AZ_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(s, &g);
-        if (rc != AZ_OK) { if (g) cudaGraphDestroy(g); return rc; }
-        if (e != cudaSuccess) return fail(AZ_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        if (e == cudaSuccess) {
+            e = cudaStreamEndCapture(cs, &g);
+            if (e != cudaSuccess && rc == AZ_OK) rc = fail(AZ_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        cudaStreamDestroy(cs);
+        if (rc != AZ_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
         P->graph = g;
         AZ_CUDA(cudaGraphInstantiate(&P->exec, g, 0));
-        return AZ_OK;  // the eager launch above produced this call's results
+        return AZ_OK;
     }
     AZ_CUDA(cudaGraphLaunch(P->exec, s));
     return AZ_OK;

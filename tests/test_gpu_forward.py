@@ -109,7 +109,7 @@ def test_batch_equals_single_frame():
     corr = c.corrections_dev()
     frames = np.stack([synth.ring_image(c.crad, seed=s, dtype=np.uint32) for s in range(11)])
     fd = to_dev(frames)
-    for fpp in (1, 2, 4, 8):
+    for fpp in (1, 2, 4, 8, 16, 32):
         gpu.set_tuning(frames_per_pass=fpp)
         out = gpu.integrate_batch(fd, *corr)
         for k in range(frames.shape[0]):
@@ -123,8 +123,8 @@ def test_batch_equals_single_frame():
         assert per <= 1e-5 and norm <= 1e-5
 
 
-@pytest.mark.parametrize("tile", [(16, 64), (32, 32), (64, 64), (16, 128)])
-@pytest.mark.parametrize("rpw", [1, 2, 4, 8])
+@pytest.mark.parametrize("tile", [(16, 64), (32, 32), (64, 64), (16, 128), (8, 256)])
+@pytest.mark.parametrize("rpw", [1, 4, 32])
 def test_tunings_give_same_answer(tile, rpw):
     w = small_workload(150, 190, split=2, npt=140, seed=41)
     c = Case(w)
@@ -134,6 +134,28 @@ def test_tunings_give_same_answer(tile, rpw):
     check_outputs(res, c.oracle(), "fp64", "tuning")
     res = gpu.integrate(c.image_dev(), *c.corrections_dev(), precision="fp32")
     check_outputs(res, c.oracle(), "fp32", "tuning")
+
+
+@pytest.mark.parametrize("tile", [(16, 128), (8, 256), (32, 64)])
+def test_copy_engines_identical(tile):
+    """TMA bulk row copies and 16-byte cp.async copies stage the same bytes: identical
+    results for the single-frame (FP64 and FP32) and batched paths."""
+    w = small_workload(143, 301, split=2, npt=130, seed=43)
+    c = Case(w, mask=random_mask(143, 301, 4))
+    gpu = c.gpu_from_oracle_positions()
+    gpu.set_tuning(tile_h=tile[0], tile_w=tile[1])
+    corr = c.corrections_dev()
+    frames = to_dev(np.stack([synth.ring_image(c.crad, seed=s, dtype=np.uint32) for s in range(9)]))
+    res = {}
+    for eng in ("tma", "async"):
+        gpu.set_copy_engine(eng)
+        a = [t.clone() for t in gpu.integrate(c.image_dev(), *corr, precision="fp64")]
+        b = [t.clone() for t in gpu.integrate(c.image_dev(), *corr, precision="fp32")]
+        o = [t.clone() for t in gpu.integrate_batch(frames, *corr)]
+        res[eng] = a + b + o
+    for x, y in zip(res["tma"], res["async"]):
+        assert torch.equal(x, y)
+    check_outputs(res["async"][:4], c.oracle(), "fp64", "engine")
 
 
 def test_batch_host_matches_device():
