@@ -295,9 +295,12 @@ int az_profile_enable(az_integrator *h, int enable);
  * clear the record. */
 int az_profile_read(az_integrator *h, az_profile *out);
 
-/* How the forward stages a pixel tile into shared memory: AZ_COPY_TMA issues one bulk
- * (cp.async.bulk) copy per tile row; AZ_COPY_ASYNC issues 16-byte cp.async copies spread
- * over a warp.  Results are identical; only speed differs. */
+/* How the forward stages a pixel tile into shared memory.  AZ_COPY_TMA (the default) loads
+ * each tile as four 2-D tensor boxes, one per class of rows with equal index mod 4 (rows of
+ * one class are 16 * width bytes apart, which meets the tensor-map stride rule for any
+ * width); it applies to tiles up to 236 pixels wide, wider tiles use AZ_COPY_ASYNC.
+ * AZ_COPY_ASYNC issues 16-byte cp.async copies spread over the producer warps.  Results are
+ * identical; only speed differs.  Defaults: 16 x 64 pixel tiles, 16 frames per pass. */
 int az_set_copy_engine(az_integrator *h, int engine);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */

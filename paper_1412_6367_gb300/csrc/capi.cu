@@ -39,13 +39,13 @@ int alloc_scratch(az_integrator *h) {
 
 int finish_build(az_integrator *h, cudaStream_t s) {
     // defaults measured on the Pilatus-6M workload; az_autotune refines them per matrix
-    int th = 16, tw = 128;
+    int th = 16, tw = 64;
     if (build_tiled_layout(h, th, tw, s) != AZ_OK) {  // a denser matrix: smaller tiles
         th = 8;
-        tw = 64;
+        tw = 32;
         AZ_TRY(build_tiled_layout(h, th, tw, s));
     }
-    h->frames_per_pass = 8;
+    h->frames_per_pass = 16;
     h->rows_per_warp = 32 / h->frames_per_pass;
     AZ_TRY(alloc_scratch(h));
     AZ_TRY(h->status.alloc(sizeof(int)));

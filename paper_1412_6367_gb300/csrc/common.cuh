@@ -77,7 +77,8 @@ struct GeomParams {
 // (tile, row, pixel); a "segment" is the run of one matrix row inside one tile.  Each
 // tile's entries start on a multiple of 8 entries so that they can be bulk-copied.
 struct TiledLayout {
-    int th = 0, tw = 0, srow = 0;      // tile rows/cols, shared-memory row stride (words)
+    int th = 0, tw = 0, srow = 0;      // tile rows/cols, shared-memory row pitch (tw + 4 words)
+    int ss = 0;                        // words per row-class slot (tile rows of equal index mod 4)
     int ntx = 0, nty = 0, ntiles = 0;  // tile grid
     int n_active = 0;                  // tiles with at least one entry
     int nseg = 0;
@@ -93,6 +94,8 @@ struct TiledLayout {
     DevBuf ent_loc;         // uint16 [padded_nnz] (shared-memory word offset in the tile)
     DevBuf ent_w32;         // float  [padded_nnz]
     DevBuf ent_w64;         // double [padded_nnz]
+    DevBuf ent_pix;         // int32  [padded_nnz] (pixel of the entry; -1 for padding)
+    DevBuf ent_dark;        // float  [padded_nnz] (dark of the entry's pixel, per batch call)
     // Per active tile: a 32-byte descriptor {tile, record offset (words), record words,
     // entry offset, padded entry count, segment count, 0, 0} and a 16-byte aligned record
     // {tile, ns, entry offset, entry count, slot[ns], uint16 start[ns + 1]} that the forward
@@ -141,7 +144,7 @@ struct az_integrator {
     azint::DevBuf csc_ptr, csc_row, csc_w64, csc_w32;
     azint::TiledLayout tl;
     // tuning
-    int rows_per_warp = 4, frames_per_pass = 8, copy_engine = AZ_COPY_ASYNC;
+    int rows_per_warp = 2, frames_per_pass = 16, copy_engine = AZ_COPY_TMA;
     // scratch: per-segment partial sums and per-row frame-independent sums
     azint::DevBuf partial;     // float or double [planes][nseg]
     size_t partial_bytes = 0;

@@ -628,7 +628,7 @@ __global__ void csr_rows_kernel(const int32_t *__restrict__ ptr, int nrows, int6
 }
 
 struct TileGeom {
-    int nx, th, tw, srow, ntx;
+    int nx, th, tw, srow, ss, ntx;
 };
 
 __device__ __forceinline__ int tile_of(const TileGeom &T, int32_t p) {
@@ -636,16 +636,20 @@ __device__ __forceinline__ int tile_of(const TileGeom &T, int32_t p) {
     return (i / T.th) * T.ntx + j / T.tw;
 }
 
-// Shared-memory word offset of pixel p inside its tile: rows of `srow` words; each row
-// starts at the misalignment of the row's first pixel modulo 16 bytes, so that the row can
-// be bulk-copied from its 16-byte aligned global address.
+// Shared-memory word offset of pixel p inside its staged tile.  Tile rows are grouped by
+// their index modulo 4 into four 128-byte aligned slots of `ss` words: rows ly = 4 jj + s sit
+// in slot s at pitch srow = tw + 20, starting c_s = (nx * s) mod 4 words into the row.  This
+// is where one 2D copy per row class (rows of equal index mod 4 are 16 * nx bytes apart, a
+// multiple of 16) puts them; the copy adds a per-plane shift of 0..15 words that depends only
+// on the plane (base address, first row, plane index), so the offset below is the same for
+// every frame.
 __device__ __forceinline__ int tile_loc(const TileGeom &T, int32_t p) {
     const int i = p / T.nx, j = p - i * T.nx;
     const int ti = i / T.th, tj = j / T.tw;
     const int ly = i - ti * T.th, lx = j - tj * T.tw;
-    const int64_t q = (int64_t)i * T.nx + (int64_t)tj * T.tw;
-    const int m0 = (int)(q & 3);
-    return ly * T.srow + m0 + lx;
+    const int sl = ly & 3, jj = ly >> 2;
+    const int cs = ((T.nx & 3) * sl) & 3;
+    return sl * T.ss + cs + jj * T.srow + lx;
 }
 
 __global__ void tile_keys_kernel(TileGeom T, const int32_t *__restrict__ idx, int64_t n,
@@ -679,6 +683,7 @@ struct TiledFillArgs {
     const double *csr_w;
     const int32_t *flag, *seg_id, *tile_unp, *tile_pad;
     uint16_t *loc;
+    int32_t *pix;
     float *w32;
     double *w64;
     int32_t *seg_start, *seg_row, *seg_tile;
@@ -696,6 +701,7 @@ __global__ void tiled_fill_kernel(TiledFillArgs A) {
         const double w = A.csr_w[k];
         A.w64[pe] = w;
         A.w32[pe] = (float)w;
+        A.pix[pe] = p;
         if (A.flag[e]) {
             const int32_t s = A.seg_id[e];
             A.seg_start[s] = (int32_t)pe;
@@ -940,12 +946,15 @@ int build_integrator(int ny, int nx, const double *rad, const double *chi, int n
 int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     TiledLayout &L = h->tl;
     const int64_t nnz = h->nnz;
+    if (th < 4 || (th % 4) != 0 || tw < 4 || (tw % 4) != 0)
+        return fail(AZ_EINVAL, "tile %dx%d: both sides must be positive multiples of 4", th, tw);
     TileGeom T;
-    T.nx = h->nx; T.th = th; T.tw = tw; T.srow = tw + 8;
+    T.nx = h->nx; T.th = th; T.tw = tw; T.srow = tw + 20;
+    T.ss = ((th / 4) * T.srow + 31) & ~31;
     T.ntx = (h->nx + tw - 1) / tw;
     const int nty = (h->ny + th - 1) / th;
     const int ntiles = T.ntx * nty;
-    if ((int64_t)th * T.srow > 65535) return fail(AZ_EINVAL, "tile %dx%d too large", th, tw);
+    if ((int64_t)4 * T.ss > 65535) return fail(AZ_EINVAL, "tile %dx%d too large", th, tw);
 
     // row of each CSR entry, tile key of each CSR entry, stable sort by tile
     DevBuf csr_row, tkey, perm;
@@ -999,9 +1008,12 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_TRY(L.ent_loc.alloc(sizeof(uint16_t) * (size_t)padded));
     AZ_TRY(L.ent_w32.alloc(sizeof(float) * (size_t)padded));
     AZ_TRY(L.ent_w64.alloc(sizeof(double) * (size_t)padded));
+    AZ_TRY(L.ent_pix.alloc(sizeof(int32_t) * (size_t)padded));
+    L.ent_dark.release();
     AZ_CUDA(cudaMemsetAsync(L.ent_loc.p, 0, L.ent_loc.bytes, s));
     AZ_CUDA(cudaMemsetAsync(L.ent_w32.p, 0, L.ent_w32.bytes, s));
     AZ_CUDA(cudaMemsetAsync(L.ent_w64.p, 0, L.ent_w64.bytes, s));
+    AZ_CUDA(cudaMemsetAsync(L.ent_pix.p, 0xff, L.ent_pix.bytes, s));  // padding entries: -1
     DevBuf seg_row, seg_tile;
     AZ_TRY(L.seg_ent_ptr.alloc(sizeof(int32_t) * 2 * (size_t)nseg));  // [start | end]
     AZ_TRY(seg_row.alloc(sizeof(int32_t) * nseg));
@@ -1012,6 +1024,7 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     A.csr_w = h->csr_w64.as<double>(); A.flag = flag.as<int32_t>(); A.seg_id = segid.as<int32_t>();
     A.tile_unp = tunp.as<int32_t>(); A.tile_pad = L.tile_ent_ptr.as<int32_t>();
     A.loc = L.ent_loc.as<uint16_t>(); A.w32 = L.ent_w32.as<float>(); A.w64 = L.ent_w64.as<double>();
+    A.pix = L.ent_pix.as<int32_t>();
     A.seg_start = L.seg_ent_ptr.as<int32_t>(); A.seg_row = seg_row.as<int32_t>();
     A.seg_tile = seg_tile.as<int32_t>(); A.n = nnz;
     AZ_TRY(launch_gs(tiled_fill_kernel, nnz, s, A));
@@ -1092,7 +1105,7 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
                      L.tile_desc.as<int32_t>()));
     AZ_CUDA(cudaStreamSynchronize(s));
 
-    L.th = th; L.tw = tw; L.srow = T.srow; L.ntx = T.ntx; L.nty = nty; L.ntiles = ntiles;
+    L.th = th; L.tw = tw; L.srow = T.srow; L.ss = T.ss; L.ntx = T.ntx; L.nty = nty; L.ntiles = ntiles;
     L.n_active = n_active; L.nseg = nseg; L.padded_nnz = padded;
     L.max_tile_entries = maxes[0]; L.max_tile_segments = maxes[1];
     L.max_rec_words = max_rec;

@@ -15,7 +15,11 @@
 // the reduction happen in the same pass (the paper's separate cast / correction / memset /
 // integrate kernels).  FP32 sums are Kahan-compensated (Sec. 5.2.2); FP64 sums are plain.
 // No atomics are used, so results are bit-reproducible run to run.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstring>
 #include <new>
 #include <vector>
 
@@ -41,7 +45,7 @@ struct Inst {
     const int32_t *seg_start, *seg_end, *seg_slot, *row_slot_ptr;
     const uint16_t *ent_loc;
     const void *ent_w;
-    int ny, nx, th, tw, srow, ntx, rpw, nseg, nrows;
+    int ny, nx, th, tw, srow, ss, ntx, rpw, nseg, nrows;
     int64_t npix;
     // inputs
     const char *img;  // first frame of this launch
@@ -57,6 +61,7 @@ struct Inst {
     int stage_entries;
     int *status;
     const int32_t *tile_desc, *tile_rec;  // per active tile: descriptor [8] and record
+    const float *ent_dark;                // frames pass: dark of each entry's pixel (or NULL)
 };
 
 struct StageGeom {
@@ -65,6 +70,7 @@ struct StageGeom {
     uint32_t ent_cap;       // entry capacity (staged entries)
     uint32_t stage_bytes;   // bytes per stage (multiple of 128)
     uint32_t rec_cap;       // bytes reserved for the tile record
+    int ent_dk;             // entries carry a staged per-entry dark (frames pass)
     int nstages;            // pipeline depth
 };
 
@@ -74,7 +80,7 @@ struct StageGeom {
 template <int MODE>
 __device__ __forceinline__ int plane_count(const Inst &d, int nimg) {
     int n = nimg;
-    if (MODE != MODE_NORM && d.dark) ++n;
+    if (MODE == MODE_SINGLE && d.dark) ++n;
     if (MODE != MODE_FRAMES) n += (d.flat != nullptr) + (d.sa != nullptr) + (d.pol != nullptr);
     return n;
 }
@@ -83,7 +89,7 @@ template <int MODE>
 __device__ __forceinline__ const char *plane_base(const Inst &d, int f0, int nimg, int pl, int &kind) {
     if (pl < nimg) { kind = 0; return d.img + (size_t)(f0 + pl) * (size_t)d.npix * 4u; }
     int k = pl - nimg;
-    if (MODE != MODE_NORM && d.dark) { if (k == 0) { kind = 1; return (const char *)d.dark; } --k; }
+    if (MODE == MODE_SINGLE && d.dark) { if (k == 0) { kind = 1; return (const char *)d.dark; } --k; }
     if (MODE != MODE_FRAMES) {
         if (d.flat) { if (k == 0) { kind = 2; return (const char *)d.flat; } --k; }
         if (d.sa) { if (k == 0) { kind = 3; return (const char *)d.sa; } --k; }
@@ -115,12 +121,16 @@ __device__ __forceinline__ TileDesc load_desc(const Inst &d, int64_t local) {
     return TileDesc{x.x, x.y, x.z, x.w, y.x, y.y};
 }
 
-// Words between two staged planes: th * srow padded to 4 (mod 32), so that the same pixel of
-// consecutive planes falls in different shared-memory banks.
-__host__ __device__ __forceinline__ uint32_t plane_stride(int th, int srow) {
-    const uint32_t p = (uint32_t)th * (uint32_t)srow;
-    return p + ((4u - p) & 31u);
-}
+// Words between two staged planes: four 128-byte aligned row-class slots.  (Planes are
+// spread over the shared-memory banks by a per-plane shift of 4 * (plane mod 4) words that
+// the copies apply, see produce().)
+__host__ __device__ __forceinline__ uint32_t plane_stride(int ss) { return 4u * (uint32_t)ss; }
+
+// Four 2D tensor maps per staged array, one per tile-row class (rows of equal index mod 4,
+// 16 * nx bytes apart).  Index: 0 image, 1 dark, 2 flat, 3 solid angle, 4 polarisation.
+struct TmaSet {
+    CUtensorMap m[5][4];
+};
 
 // Stage layout: [header 256 B][tile record][planes][entry locs][entry weights].
 // Header ints: 0 ns, 1 group, 2 nimg, 3..6 word offsets of dark, flat, solid angle,
@@ -135,25 +145,35 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Producer warps: stage work item `local` of instance d.  Warp 0 writes the item header,
-// bulk-copies (TMA) the tile record and entries, and -- with the TMA engine -- one bulk copy
-// per tile row of every plane.  With the cp.async engine all producer warps copy the plane
-// rows in 16-byte pieces, eight lanes per row, which sustains bandwidth on short rows.
-// Every producer thread makes exactly one arrival per item (deferred until its cp.async
-// copies land), and lane 0 of warp 0 one more after publishing the header: kFullCount.
+// Producer warps: stage work item `local` of instance d.  Warp 0 writes the item header and
+// bulk-copies (TMA) the tile record and entries.  Each plane of the tile is staged as four
+// row classes (tile rows of equal index mod 4, which are 16 * nx bytes apart in global
+// memory): with the TMA engine one 2D tensor copy per class -- a box of srow x (th / 4)
+// words into a 128-byte aligned slot -- and with the cp.async engine the same words in
+// 16-byte pieces spread over all producer lanes.  For a plane whose base address is beta
+// words mod 4 and whose first tile row is global row g0, class k goes to slot
+// s = (k - g0) mod 4, and the box starts at column X = c0 - 4 (flag + spread) where
+// off_k = (beta + k nx) mod 4, c_s = (nx s) mod 4, phi = (beta + nx g0) mod 4,
+// flag = (c_s + phi - off_k) / 4 in {0, 1} and spread = plane mod 4.  Pixel (ly, c0 + lx)
+// then sits at the build-time offset plus phi + 4 spread, the per-plane shift the consumers
+// add.  Every producer thread makes one arrival per item (deferred until its cp.async copies
+// land) and lane 0 of warp 0 one more after publishing the header: kFullCount arrivals.
 template <int MODE, class WT, bool TMA>
-__device__ void produce(const Inst &d, int64_t local, const TileDesc &td, unsigned char *stage,
-                        const StageGeom &sg, uint64_t *bar, int *ctr, int pwarp) {
+__device__ void produce(const Inst &d, const TmaSet &tm, int64_t local, const TileDesc &td,
+                        unsigned char *stage, const StageGeom &sg, uint64_t *bar, int *ctr,
+                        int pwarp) {
     const int lane = threadIdx.x & 31;
     const int group = (int)(local % d.n_groups);
     const int t = td.t;
     const int ti = t / d.ntx, tj = t - ti * d.ntx;
     const int r0 = ti * d.th, c0 = tj * d.tw;
-    const int rows = min(d.th, d.ny - r0), tweff = min(d.tw, d.nx - c0);
     const int f0 = group * d.fpi;
     const int nimg = MODE == MODE_SINGLE ? 1 : (MODE == MODE_FRAMES ? min(d.fpi, d.n_frames - f0) : 0);
     const int np = plane_count<MODE>(d, nimg);
-    const uint32_t pw = plane_stride(d.th, d.srow);
+    const uint32_t pw = plane_stride(d.ss);
+    const int nu = d.nx & 3;
+    const int rows4 = d.th >> 2;          // rows per class in a tile
+    const int boxw = d.srow;              // words per staged row (tw + 20)
     unsigned char *rec_dst = stage + kHeaderBytes;
     uint32_t *planes = reinterpret_cast<uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
     unsigned char *eloc = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
@@ -161,21 +181,42 @@ __device__ void produce(const Inst &d, int64_t local, const TileDesc &td, unsign
     const uint32_t ne = (uint32_t)td.ne;
     const bool stage_e = d.stage_entries != 0;
 
+    // plane geometry: array base, first global row of the tile in that array, rows in it
+    auto plane_geo = [&](int pl, const char *&arr, int64_t &g0, int64_t &rows_total, int &kind) {
+        if (pl < nimg) {
+            kind = 0;
+            arr = d.img;
+            g0 = (int64_t)(f0 + pl) * d.ny + r0;
+            rows_total = (int64_t)d.n_frames * d.ny;
+        } else {
+            plane_base<MODE>(d, f0, nimg, pl, kind);
+            arr = kind == 1 ? (const char *)d.dark : kind == 2 ? (const char *)d.flat
+                : kind == 3 ? (const char *)d.sa : (const char *)d.pol;
+            g0 = r0;
+            rows_total = d.ny;
+        }
+    };
+
     if (pwarp == 0) {
         uint32_t mine = 0;
         if (TMA) {
-            for (int pl = 0; pl < np; ++pl) {
+            // lane pl * 4 + k copies class k of plane pl
+            for (int job = lane; job < 4 * np; job += 32) {
+                const int pl = job >> 2, k = job & 3;
+                const char *arr;
+                int64_t g0, rows_total;
                 int kind;
-                const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
-                for (int ly = lane; ly < rows; ly += 32) {
-                    const uintptr_t src = b + 4u * (uintptr_t)((int64_t)(r0 + ly) * d.nx + c0);
-                    mine += (uint32_t)(((src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15) - (src & ~(uintptr_t)15));
-                }
+                plane_geo(pl, arr, g0, rows_total, kind);
+                const int phi = (int)(g0 & 3);
+                const int sl = (k - phi) & 3;
+                if (g0 + sl < rows_total) mine += (uint32_t)(boxw * rows4 * 4);
             }
         }
+        const bool dk = MODE == MODE_FRAMES && d.ent_dark != nullptr && stage_e;
         if (lane == 0) {
             mine += (uint32_t)td.rec_words * 4u;
             if (stage_e) mine += ne * 2u + ne * (uint32_t)sizeof(WT);
+            if (dk) mine += ne * 4u;
         }
         fence_proxy_async_smem();
         if (mine)
@@ -188,40 +229,68 @@ __device__ void produce(const Inst &d, int64_t local, const TileDesc &td, unsign
                 bulk_g2s(eloc, d.ent_loc + td.e_off, ne * 2u, bar);
                 bulk_g2s(ew, static_cast<const WT *>(d.ent_w) + td.e_off, ne * (uint32_t)sizeof(WT), bar);
             }
+            if (dk && ne) bulk_g2s(ew + sg.ent_cap * (uint32_t)sizeof(WT), d.ent_dark + td.e_off, ne * 4u, bar);
         }
         if (TMA) {
-            for (int pl = 0; pl < np; ++pl) {
+            for (int job = lane; job < 4 * np; job += 32) {
+                const int pl = job >> 2, k = job & 3;
+                const char *arr;
+                int64_t g0, rows_total;
                 int kind;
-                const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
-                const int dlt = (int)((b >> 2) & 3u);
-                for (int ly = lane; ly < rows; ly += 32) {
-                    const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
-                    const uintptr_t src = b + 4u * (uintptr_t)q;
-                    const uintptr_t lo = src & ~(uintptr_t)15;
-                    const uintptr_t hi = (src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15;
-                    const int dst_off = ((int)(q & 3) + dlt) >= 4 ? 4 : 0;
-                    bulk_g2s(planes + (size_t)pl * pw + (size_t)ly * d.srow + dst_off,
-                             reinterpret_cast<const void *>(lo), (uint32_t)(hi - lo), bar);
-                }
+                plane_geo(pl, arr, g0, rows_total, kind);
+                const int beta = (int)((reinterpret_cast<uintptr_t>(arr) >> 2) & 3u);
+                const int phi_row = (int)(g0 & 3);
+                const int sl = (k - phi_row) & 3;
+                if (g0 + sl >= rows_total) continue;
+                const int phi = (beta + nu * phi_row) & 3;
+                const int offk = (beta + k * nu) & 3;
+                const int cs = (nu * sl) & 3;
+                const int flag = (cs + phi - offk) >> 2;
+                const int x = c0 - 4 * (flag + (pl & 3));
+                uint32_t *dst = planes + (size_t)pl * pw + (size_t)sl * d.ss;
+                const int y = (int)((g0 + sl - k) >> 2);
+                const CUtensorMap *map = &tm.m[kind][k];
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                    " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+                    "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+                    : "memory");
             }
         }
     }
     if (!TMA) {
-        // eight lanes per row, four rows per warp, rows spread over the producer warps
+        // the same words as the tensor copies: for every (plane, class, row in class) a run of
+        // boxw / 4 16-byte pieces from column c0 - off_k; eight lanes per run
         const int sub = lane >> 3, l8 = lane & 7;
-        for (int pl = 0; pl < np; ++pl) {
+        const int runs = np * 4 * rows4;
+        const int nchunk = boxw >> 2;
+        for (int r = pwarp * 4 + sub; r < runs; r += 4 * kProducers) {
+            const int pl = r / (4 * rows4);
+            const int rem = r - pl * 4 * rows4;
+            const int k = rem / rows4, jj = rem - k * rows4;
+            const char *arr;
+            int64_t g0, rows_total;
             int kind;
-            const uintptr_t b = reinterpret_cast<uintptr_t>(plane_base<MODE>(d, f0, nimg, pl, kind));
-            const int dlt = (int)((b >> 2) & 3u);
-            for (int ly = pwarp * 4 + sub; ly < rows; ly += 4 * kProducers) {
-                const int64_t q = (int64_t)(r0 + ly) * d.nx + c0;
-                const uintptr_t src = b + 4u * (uintptr_t)q;
-                const uintptr_t lo = src & ~(uintptr_t)15;
-                const int nch = (int)((((src + 4u * (uintptr_t)tweff + 15u) & ~(uintptr_t)15) - lo) >> 4);
-                const int dst_off = ((int)(q & 3) + dlt) >= 4 ? 4 : 0;
-                uint32_t *dst = planes + (size_t)pl * pw + (size_t)ly * d.srow + dst_off;
-                for (int c = l8; c < nch; c += 8)
-                    cp_async16(dst + 4 * c, reinterpret_cast<const void *>(lo + 16u * (uintptr_t)c));
+            plane_geo(pl, arr, g0, rows_total, kind);
+            const int beta = (int)((reinterpret_cast<uintptr_t>(arr) >> 2) & 3u);
+            const int phi_row = (int)(g0 & 3);
+            const int sl = (k - phi_row) & 3;
+            const int64_t g = g0 + sl + 4 * (int64_t)jj;  // global row of this run
+            if (g >= rows_total) continue;
+            const int phi = (beta + nu * phi_row) & 3;
+            const int offk = (beta + k * nu) & 3;
+            const int cs = (nu * sl) & 3;
+            const int flag = (cs + phi - offk) >> 2;
+            const int x = c0 - 4 * (flag + (pl & 3));
+            uint32_t *dst = planes + (size_t)pl * pw + (size_t)sl * d.ss + (size_t)jj * boxw;
+            const int64_t e0 = g * d.nx + x - offk;       // first element of the run (in the array)
+            const int64_t elems = rows_total * d.nx;
+            const char *src = arr + 4 * e0;               // 16-byte aligned by construction
+            for (int c = l8; c < nchunk; c += 8) {
+                // copy every piece that overlaps the array; a piece is 16-byte aligned, so the
+                // words it holds outside the array share a 16-byte granule with one inside it
+                const int64_t ec = e0 + 4 * c;
+                if (ec + 3 >= 0 && ec < elems) cp_async16(dst + 4 * c, src + 16 * c);
             }
         }
         cp_async_arrive(bar);  // deferred arrival when this thread's copies have landed
@@ -233,9 +302,13 @@ __device__ void produce(const Inst &d, int64_t local, const TileDesc &td, unsign
         h[0] = td.ns; h[1] = group; h[2] = nimg; h[3] = h[4] = h[5] = h[6] = -1;
         h[7] = t; h[8] = td.e_off;
         for (int pl = 0; pl < np; ++pl) {
+            const char *arr;
+            int64_t g0, rows_total;
             int kind;
-            const char *b = plane_base<MODE>(d, f0, nimg, pl, kind);
-            const int o = (int)(pl * pw + ((reinterpret_cast<uintptr_t>(b) >> 2) & 3u));
+            plane_geo(pl, arr, g0, rows_total, kind);
+            const int beta = (int)((reinterpret_cast<uintptr_t>(arr) >> 2) & 3u);
+            const int phi = (beta + nu * (int)(g0 & 3)) & 3;
+            const int o = (int)(pl * pw + phi + 4 * (pl & 3));
             if (kind == 0) h[16 + pl] = o; else h[2 + kind] = o;
         }
         *ctr = 0;          // segment claim counter of this stage
@@ -290,22 +363,40 @@ struct ConsumerParams {
     void *partial;
     const uint16_t *ent_loc;
     const void *ent_w;
+    const float *ent_dark;
     int nseg, fpi, stage_entries;
 };
 
 __device__ __forceinline__ ConsumerParams consumer_params(const Inst &d) {
-    return ConsumerParams{d.partial, d.ent_loc, d.ent_w, d.nseg, d.fpi, d.stage_entries};
+    return ConsumerParams{d.partial, d.ent_loc, d.ent_w, d.ent_dark, d.nseg, d.fpi, d.stage_entries};
 }
 
+template <class WT> struct W4;
+template <> struct W4<float> {
+    static __device__ __forceinline__ void load(const float *p, float w[4]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+};
+template <> struct W4<double> {
+    static __device__ __forceinline__ void load(const double *p, double w[4]) {
+        const double2 a = *reinterpret_cast<const double2 *>(p);
+        const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+        w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+    }
+};
+
 // One lane per (segment, quantity).  A warp takes 32 / Q segments at a time from the stage's
-// claim counter; the Q lanes of a segment share its (loc, weight) stream (broadcast reads)
-// and each sums one quantity over all of the segment's entries, in entry order:
+// claim counter; the Q lanes of a segment share its entry stream (broadcast reads) and each
+// sums one quantity over all of the segment's entries:
 //   frames pass: quantity q = frame q of the item, value = cast(image) - dark;
 //   norm pass:   q = 0: flat * solid angle * polarisation, q = 1: 1 (the count);
 //   single pass: q = 0: cast(image) - dark, q = 1: the normalisation, q = 2: 1, q = 3 idle.
-// Every quantity of every pass is reduced by the same sequence of operations, so a flat
-// image with unit corrections gives S == N bit for bit, and a frame integrated alone or in
-// a batch gives the same bits.  No merge between lanes is needed.
+// Entries are read four at a time from 4-aligned positions (one 8-byte read of the locations,
+// 16-byte reads of the weights and per-entry darks); entry e goes to accumulator e mod 4 and
+// the four are combined as ((a0 + a1) + (a2 + a3)).  Every quantity of every pass is reduced
+// by this same sequence of operations, so a flat image with unit corrections gives S == N bit
+// for bit, and a frame integrated alone or in a batch gives the same bits.
 template <int Q, class AT, class WT, int MODE, int DT, bool SE>
 __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *stage,
                                const StageGeom &sg, int *ctr) {
@@ -315,7 +406,6 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
     const int *h = reinterpret_cast<const int *>(stage);
     const int ns = h[0], group = h[1], nimg = h[2];
     const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
-    // this lane's image plane (frames / single passes)
     const int oimg = h[16 + (MODE == MODE_FRAMES ? q : 0)];
     bool active;
     if (MODE == MODE_FRAMES) active = q < nimg;
@@ -326,14 +416,18 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
     const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
     const uint16_t *L;
     const WT *W;
+    const float *DK;
     if constexpr (SE) {
-        L = reinterpret_cast<const uint16_t *>(stage + kHeaderBytes + sg.rec_cap + sg.plane_region);
-        W = reinterpret_cast<const WT *>(stage + kHeaderBytes + sg.rec_cap + sg.plane_region + sg.ent_cap * 2u);
+        const unsigned char *eb = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
+        L = reinterpret_cast<const uint16_t *>(eb);
+        W = reinterpret_cast<const WT *>(eb + sg.ent_cap * 2u);
+        DK = reinterpret_cast<const float *>(eb + sg.ent_cap * (2u + (uint32_t)sizeof(WT)));
     } else {
         L = cp.ent_loc + h[8];
         W = static_cast<const WT *>(cp.ent_w) + h[8];
+        DK = cp.ent_dark ? cp.ent_dark + h[8] : nullptr;
     }
-    // output row of this lane's quantity in the partial buffer
+    const bool has_dk = MODE == MODE_FRAMES && sg.ent_dk;
     size_t orow;
     if (MODE == MODE_FRAMES) orow = (size_t)(group * cp.fpi + q) * cp.nseg;
     else orow = (size_t)q * cp.nseg;
@@ -351,61 +445,58 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
             slot = slots[sl];
         }
         if (!active) e1 = e0;
-        // four independent sums per lane (entries e0 + 4k + j in sum j), combined in a fixed
-        // order: ((a0 + a1) + (a2 + a3))
         Acc<AT> acc[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[j].zero();
-        auto value_of = [&](int e, AT &w, AT &x) {
-            const int loc = L[e];
-            w = (AT)W[e];
-            if (MODE == MODE_FRAMES) {
-                float v = img_f32<DT>(planes[oimg + loc]);
-                if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc]));
-                x = (AT)v;
-            } else if (MODE == MODE_NORM) {
-                AT n = AT(1);
-                if (q == 0) {
-                    if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
-                    if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
-                    if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
-                }
-                x = n;
-            } else {
-                if (q == 0) {
-                    if (sizeof(AT) == 8) {
-                        x = (AT)img_f64<DT>(planes[oimg + loc]);
-                        if (odark >= 0) x = x - (AT)__uint_as_float(planes[odark + loc]);
-                    } else {
-                        float v = img_f32<DT>(planes[oimg + loc]);
-                        if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc]));
-                        x = (AT)v;
-                    }
-                } else if (q == 1) {
+        for (int qd = e0 & ~3; qd < e1; qd += 4) {
+            const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
+            const int loc[4] = {(int)(l2.x & 0xffffu), (int)(l2.x >> 16), (int)(l2.y & 0xffffu),
+                                (int)(l2.y >> 16)};
+            WT w[4];
+            W4<WT>::load(W + qd, w);
+            float dk[4] = {0.f, 0.f, 0.f, 0.f};
+            if (has_dk) {
+                const float4 v = *reinterpret_cast<const float4 *>(DK + qd);
+                dk[0] = v.x; dk[1] = v.y; dk[2] = v.z; dk[3] = v.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int e = qd + j;
+                if (e < e0 || e >= e1) continue;
+                AT x;
+                if (MODE == MODE_FRAMES) {
+                    float v = img_f32<DT>(planes[oimg + loc[j]]);
+                    if (has_dk) v = __fsub_rn(v, dk[j]);
+                    x = (AT)v;
+                } else if (MODE == MODE_NORM) {
                     AT n = AT(1);
-                    if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
-                    if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
-                    if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
+                    if (q == 0) {
+                        if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc[j]]);
+                        if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc[j]]);
+                        if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc[j]]);
+                    }
                     x = n;
                 } else {
-                    x = AT(1);
+                    if (q == 0) {
+                        if (sizeof(AT) == 8) {
+                            x = (AT)img_f64<DT>(planes[oimg + loc[j]]);
+                            if (odark >= 0) x = x - (AT)__uint_as_float(planes[odark + loc[j]]);
+                        } else {
+                            float v = img_f32<DT>(planes[oimg + loc[j]]);
+                            if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc[j]]));
+                            x = (AT)v;
+                        }
+                    } else if (q == 1) {
+                        AT n = AT(1);
+                        if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc[j]]);
+                        if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc[j]]);
+                        if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc[j]]);
+                        x = n;
+                    } else {
+                        x = AT(1);
+                    }
                 }
-            }
-        };
-        int e = e0;
-        for (; e + 4 <= e1; e += 4) {
-            AT w[4], x[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) value_of(e + j, w[j], x[j]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j].add(w[j], x[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (e + j < e1) {
-                AT w, x;
-                value_of(e + j, w, x);
-                acc[j].add(w, x);
+                acc[j].add((AT)w[j], x);
             }
         }
         acc[0].merge(acc[1]);
@@ -433,8 +524,11 @@ __device__ __forceinline__ void consume_dispatch(const ConsumerParams &cp, const
 template <class AT, class WT, int MODE, int NIMG, int DT, bool TMA>
 __global__ void __launch_bounds__(kThreads, 1)
 phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ multi, int n_inst,
-              int64_t n_items, StageGeom sg) {
-    extern __shared__ __align__(128) unsigned char smem[];
+              int64_t n_items, StageGeom sg, const __grid_constant__ TmaSet tm) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // tensor copies want 128-byte aligned destinations: align explicitly (128 bytes of slack)
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127u) & ~static_cast<uintptr_t>(127u));
     const int S = sg.nstages;
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)S * sg.stage_bytes);
     uint64_t *empty = full + S;
@@ -482,8 +576,8 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
                 break;
             }
             const Inst &d = inst_of(single, multi, n_inst, item);
-            produce<MODE, WT, TMA>(d, item - d.item_begin, td, smem + (size_t)s * sg.stage_bytes, sg,
-                                   &full[s], &ctr[s], warp);
+            produce<MODE, WT, TMA>(d, tm, item - d.item_begin, td, smem + (size_t)s * sg.stage_bytes,
+                                   sg, &full[s], &ctr[s], warp);
             td = tn;
         }
     } else {
@@ -590,15 +684,18 @@ int g_max_smem = 0;
 
 // Stage dimensions: plane slots of `plane_words` words, `planes` of them, plus (when the
 // entries are staged) room for `ent_cap` entries of (uint16 loc, wbytes weight).
-constexpr uint32_t kBarrierBytes = 256;  // full/empty barriers, claim counters, abort flag
+constexpr uint32_t kBarrierBytes = 256 + 128;  // barriers, counters, abort flag; alignment slack
 
-StageGeom stage_geom(uint32_t plane_words, int planes, uint32_t ent_cap, int wbytes, uint32_t rec_words) {
+StageGeom stage_geom(uint32_t plane_words, int planes, uint32_t ent_cap, int wbytes, uint32_t rec_words,
+                     int ent_dk = 0) {
     StageGeom sg;
     sg.plane_words = plane_words;
     sg.plane_region = (uint32_t)planes * plane_words * 4u;
     sg.ent_cap = ent_cap;
-    sg.rec_cap = (rec_words * 4u + 15u) & ~15u;
-    uint32_t bytes = kHeaderBytes + sg.rec_cap + sg.plane_region + ent_cap * (2u + (uint32_t)wbytes);
+    sg.ent_dk = ent_dk;
+    sg.rec_cap = (rec_words * 4u + 127u) & ~127u;  // keeps the plane region 128-byte aligned
+    uint32_t bytes = kHeaderBytes + sg.rec_cap + sg.plane_region +
+                     ent_cap * (2u + (uint32_t)wbytes + (ent_dk ? 4u : 0u));
     sg.stage_bytes = (bytes + 127u) & ~127u;
     // as many stages as fit (at least two, at most kMaxStages)
     const int avail = max_smem_per_block() - (int)kBarrierBytes;
@@ -611,14 +708,14 @@ uint32_t smem_for(const StageGeom &sg) { return (uint32_t)sg.nstages * sg.stage_
 // Stage the entries when the largest tile fits twice next to the planes; otherwise the
 // reduction reads the entries from global memory.
 StageGeom choose_stage(uint32_t plane_words, int planes, uint32_t max_entries, int wbytes,
-                       uint32_t rec_words, int &stage_entries) {
-    StageGeom sg = stage_geom(plane_words, planes, max_entries, wbytes, rec_words);
+                       uint32_t rec_words, int &stage_entries, int ent_dk = 0) {
+    StageGeom sg = stage_geom(plane_words, planes, max_entries, wbytes, rec_words, ent_dk);
     if ((int)smem_for(sg) <= max_smem_per_block()) {
         stage_entries = 1;
         return sg;
     }
     stage_entries = 0;
-    return stage_geom(plane_words, planes, 0, wbytes, rec_words);
+    return stage_geom(plane_words, planes, 0, wbytes, rec_words, ent_dk);
 }
 
 Inst make_inst(const az_integrator *h, bool fp64) {
@@ -633,7 +730,7 @@ Inst make_inst(const az_integrator *h, bool fp64) {
     d.row_slot_ptr = L.row_slot_ptr.as<int32_t>();
     d.ent_loc = L.ent_loc.as<uint16_t>();
     d.ent_w = fp64 ? (const void *)L.ent_w64.p : (const void *)L.ent_w32.p;
-    d.ny = h->ny; d.nx = h->nx; d.th = L.th; d.tw = L.tw; d.srow = L.srow; d.ntx = L.ntx;
+    d.ny = h->ny; d.nx = h->nx; d.th = L.th; d.tw = L.tw; d.srow = L.srow; d.ss = L.ss; d.ntx = L.ntx;
     d.rpw = 32 / h->frames_per_pass; d.nseg = L.nseg; d.nrows = h->nrows;
     d.npix = (int64_t)h->ny * h->nx;
     d.n_frames = 1; d.fpi = 1; d.n_groups = 1;
@@ -666,7 +763,7 @@ struct ProfScope {
 
 template <class AT, class WT, int MODE, int NIMG, int DT, bool TMA>
 int run_phase1(const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
-               const StageGeom &sg, cudaStream_t s, Profiler *prof = nullptr) {
+               const StageGeom &sg, const TmaSet &tm, cudaStream_t s, Profiler *prof = nullptr) {
     if (n_items <= 0) return AZ_OK;
     const uint32_t smem = smem_for(sg);
     if ((int)smem > max_smem_per_block())
@@ -680,7 +777,7 @@ int run_phase1(const Inst &single, const Inst *multi, int n_inst, int64_t n_item
     const int64_t grid = std::min<int64_t>(n_items, (int64_t)num_sms() * per_sm);
     {
         ProfScope ps(prof, MODE == MODE_FRAMES ? 0 : (MODE == MODE_NORM ? 1 : 2), s);
-        kern<<<(unsigned)grid, kThreads, smem, s>>>(single, multi, n_inst, n_items, sg);
+        kern<<<(unsigned)grid, kThreads, smem, s>>>(single, multi, n_inst, n_items, sg, tm);
     }
     AZ_CUDA(cudaGetLastError());
     return AZ_OK;
@@ -704,26 +801,102 @@ int run_phase2(const Inst &single, const Inst *multi, int n_inst, int64_t n_jobs
 
 template <class AT, class WT, int MODE, int NIMG, int DT>
 int run_phase1_eng(int engine, const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
-                   const StageGeom &sg, cudaStream_t s, Profiler *prof) {
+                   const StageGeom &sg, const TmaSet &tm, cudaStream_t s, Profiler *prof) {
     if (engine == AZ_COPY_ASYNC)
-        return run_phase1<AT, WT, MODE, NIMG, DT, false>(single, multi, n_inst, n_items, sg, s, prof);
-    return run_phase1<AT, WT, MODE, NIMG, DT, true>(single, multi, n_inst, n_items, sg, s, prof);
+        return run_phase1<AT, WT, MODE, NIMG, DT, false>(single, multi, n_inst, n_items, sg, tm, s, prof);
+    return run_phase1<AT, WT, MODE, NIMG, DT, true>(single, multi, n_inst, n_items, sg, tm, s, prof);
 }
 
 template <class AT, class WT, int MODE, int NIMG>
 int run_phase1_dt(int dtype, int engine, const Inst &single, const Inst *multi, int n_inst,
-                  int64_t n_items, const StageGeom &sg, cudaStream_t s, Profiler *prof = nullptr) {
+                  int64_t n_items, const StageGeom &sg, const TmaSet &tm, cudaStream_t s,
+                  Profiler *prof = nullptr) {
     switch (dtype) {
         case AZ_DTYPE_F32:
-            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_F32>(engine, single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_F32>(engine, single, multi, n_inst, n_items, sg, tm, s, prof);
         case AZ_DTYPE_U32:
-            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_U32>(engine, single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_U32>(engine, single, multi, n_inst, n_items, sg, tm, s, prof);
         default:
-            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_I32>(engine, single, multi, n_inst, n_items, sg, s, prof);
+            return run_phase1_eng<AT, WT, MODE, NIMG, AZ_DTYPE_I32>(engine, single, multi, n_inst, n_items, sg, tm, s, prof);
     }
 }
 
-uint32_t plane_words_of(const az_integrator *h) { return plane_stride(h->tl.th, h->tl.srow); }
+// Dark of each tiled entry's pixel (0 for padding entries), gathered once per batch call.
+__global__ void gather_dark_kernel(const int32_t *__restrict__ pix, const float *__restrict__ dark,
+                                   int64_t n, float *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = pix[e];
+        out[e] = p >= 0 ? dark[p] : 0.f;
+    }
+}
+
+// ---- tensor maps for the TMA engine --------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encoder() {
+    if (g_encode) return AZ_OK;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+        return fail(AZ_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    return AZ_OK;
+}
+
+// Four maps over `rows_total` rows of nx 4-byte words starting at `arr`: map k covers rows
+// g = 4 y + k (16 * nx bytes apart) from the 16-byte aligned address just before row k, so
+// that element (x, y) is column x - off_k of row g, off_k = (beta + k nx) mod 4.  Reads
+// outside [0, nx + off_k) x [0, rows of class k) return zeros, so no copy reads past a row or
+// the array.
+int encode_class_maps(const void *arr, int64_t rows_total, int nx, int box_w, int box_h,
+                      CUtensorMap out[4]) {
+    AZ_TRY(get_encoder());
+    const uintptr_t base = reinterpret_cast<uintptr_t>(arr);
+    const int beta = (int)((base >> 2) & 3u), nu = nx & 3;
+    for (int k = 0; k < 4; ++k) {
+        const int offk = (beta + k * nu) & 3;
+        const int64_t rows_k = rows_total > k ? (rows_total - k + 3) / 4 : 0;
+        if (rows_k == 0) {
+            memset(&out[k], 0, sizeof(CUtensorMap));  // never used: the producer skips the class
+            continue;
+        }
+        void *basek = reinterpret_cast<void *>(base + 4u * (uintptr_t)k * (uintptr_t)nx - 4u * (uintptr_t)offk);
+        cuuint64_t dims[2] = {(cuuint64_t)(nx + offk), (cuuint64_t)rows_k};
+        cuuint64_t strides[1] = {(cuuint64_t)16 * (cuuint64_t)nx};
+        cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = g_encode(&out[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, basek, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(AZ_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return AZ_OK;
+}
+
+// The engine a launch really uses: the TMA engine needs boxes of at most 256 words.
+int engine_for(const az_integrator *h) {
+    if (h->copy_engine == AZ_COPY_TMA && h->tl.srow <= 256) return AZ_COPY_TMA;
+    return AZ_COPY_ASYNC;
+}
+
+// Maps for the arrays a launch stages (image rows_img rows from img; corrections ny rows).
+int make_maps(const az_integrator *h, int engine, const void *img, int64_t rows_img, const float *dark,
+              const float *flat, const float *sa, const float *pol, TmaSet &tm) {
+    memset(&tm, 0, sizeof(tm));
+    if (engine != AZ_COPY_TMA) return AZ_OK;
+    const int bw = h->tl.srow, bh = h->tl.th / 4;
+    const void *arrs[5] = {img, dark, flat, sa, pol};
+    for (int i = 0; i < 5; ++i) {
+        if (!arrs[i]) continue;
+        AZ_TRY(encode_class_maps(arrs[i], i == 0 ? rows_img : h->ny, h->nx, bw, bh, tm.m[i]));
+    }
+    return AZ_OK;
+}
+
+uint32_t plane_words_of(const az_integrator *h) { return plane_stride(h->tl.ss); }
 uint32_t rec_words_of(const az_integrator *h) { return (uint32_t)h->tl.max_rec_words; }
 
 }  // namespace
@@ -759,12 +932,14 @@ int forward_single(const az_integrator *h, const void *image, int dtype, const f
     const int planes = 1 + (dark != nullptr) + (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries,
                                 fp64 ? 8 : 4, rec_words_of(h), d.stage_entries);
-    const int eng = h->copy_engine;
+    const int eng = engine_for(h);
+    TmaSet tm;
+    AZ_TRY(make_maps(h, eng, image, h->ny, dark, flat, sa, pol, tm));
     if (fp64) {
-        AZ_TRY((run_phase1_dt<double, double, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+        AZ_TRY((run_phase1_dt<double, double, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof)));
         AZ_TRY((run_phase2<double, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     } else {
-        AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+        AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof)));
         AZ_TRY((run_phase2<float, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     }
     return AZ_OK;
@@ -778,29 +953,45 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
     const int planes = (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
                                 rec_words_of(h), d.stage_entries);
-    AZ_TRY((run_phase1_eng<float, float, MODE_NORM, 1, AZ_DTYPE_F32>(h->copy_engine, d, nullptr, 1, d.n_items, sg, s, &h->prof)));
+    const int eng = engine_for(h);
+    TmaSet tm;
+    AZ_TRY(make_maps(h, eng, nullptr, 0, nullptr, flat, sa, pol, tm));
+    AZ_TRY((run_phase1_eng<float, float, MODE_NORM, 1, AZ_DTYPE_F32>(eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof)));
     AZ_TRY((run_phase2<float, MODE_NORM>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
     return AZ_OK;
 }
 
 int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
                  float *oI, float *oS, int frame_out0, cudaStream_t s) {
-    // frames per pass as tuned, halved while two stages of that many frame planes do not fit
+    // the dark of every entry, in entry order, so that the frames pass reads it with the
+    // weights instead of staging a dark plane with every group of frames
+    const int ent_dk = dark != nullptr;
+    if (ent_dk) {
+        TiledLayout &L = h->tl;
+        if (L.ent_dark.bytes < sizeof(float) * (size_t)L.padded_nnz)
+            AZ_TRY(L.ent_dark.alloc(sizeof(float) * (size_t)L.padded_nnz));
+        const int64_t blocks = std::min<int64_t>((L.padded_nnz + 255) / 256, (int64_t)num_sms() * 8);
+        gather_dark_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+            L.ent_pix.as<int32_t>(), dark, L.padded_nnz, L.ent_dark.as<float>());
+        AZ_CUDA(cudaGetLastError());
+    }
+    // frames per pass as tuned, halved while two stages of that many frame planes do not fit,
+    // or while the tile's entries would not fit beside them (down to 4 frames per pass)
     int fpi = h->frames_per_pass;
     while (fpi > 1) {
         int se = 0;
-        const StageGeom g = choose_stage(plane_words_of(h), fpi + (dark != nullptr),
-                                         (uint32_t)h->tl.max_tile_entries, 4, rec_words_of(h), se);
-        if ((int)smem_for(g) <= max_smem_per_block()) break;
+        const StageGeom g = choose_stage(plane_words_of(h), fpi, (uint32_t)h->tl.max_tile_entries, 4,
+                                         rec_words_of(h), se, ent_dk);
+        if ((int)smem_for(g) <= max_smem_per_block() && (se || fpi <= 4)) break;
         fpi >>= 1;
     }
     const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(h->tl.nseg, 1)));
     const int chunk_max = (int)std::max<int64_t>(fpi, (cap / fpi) * fpi);
-    const int planes = fpi + (dark != nullptr);
+    const int planes = fpi;
     int stage_e = 0;
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
-                                rec_words_of(h), stage_e);
-    const int eng = h->copy_engine;
+                                rec_words_of(h), stage_e, ent_dk);
+    const int eng = engine_for(h);
     for (int f0 = 0; f0 < n; f0 += chunk_max) {
         const int nf = std::min(chunk_max, n - f0);
         Inst d = make_inst(h, false);
@@ -808,16 +999,19 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
         d.n_frames = nf; d.fpi = fpi; d.n_groups = (nf + fpi - 1) / fpi;
         d.rpw = 32 / fpi;
         d.dark = dark;
+        d.ent_dark = ent_dk ? h->tl.ent_dark.as<float>() : nullptr;
         d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
         d.stage_entries = stage_e;
         d.n_items = h->tl.n_active * d.n_groups;
+        TmaSet tm;
+        AZ_TRY(make_maps(h, eng, d.img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
         switch (fpi) {
-            case 1: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 2: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 2>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 4: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 4>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 8: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 8>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            case 16: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 16>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
-            default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 32>(dtype, eng, d, nullptr, 1, d.n_items, sg, s, &h->prof))); break;
+            case 1: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
+            case 2: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 2>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
+            case 4: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 4>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
+            case 8: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 8>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
+            case 16: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 16>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
+            default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 32>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
         }
         AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
     }
@@ -855,7 +1049,7 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
     P->dtype = dtype;
     int64_t items = 0, rows = 0;
     uint32_t pw = 0, ecap = 0, rw = 0;
-    P->engine = hs[0]->copy_engine;
+    P->engine = AZ_COPY_ASYNC;  // one launch over many arrays: no per-array tensor maps
     int planes = 0;
     for (int k = 0; k < n; ++k) {
         const az_integrator *h = hs[k];
@@ -901,7 +1095,8 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
 int multi_enqueue(void *plan, cudaStream_t s) {
     MultiPlan *P = static_cast<MultiPlan *>(plan);
     const Inst *dev = P->dev.as<Inst>();
-    AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(P->dtype, P->engine, P->host[0], dev, P->n, P->n_items, P->sg, s)));
+    static TmaSet no_maps;  // zero: the cp.async engine does not read tensor maps
+    AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(P->dtype, P->engine, P->host[0], dev, P->n, P->n_items, P->sg, no_maps, s)));
     AZ_TRY((run_phase2<float, MODE_SINGLE>(P->host[0], dev, P->n, P->n_rows, 1, s)));
     return AZ_OK;
 }
