@@ -198,6 +198,35 @@ int az_integrate2d(const az_integrator *h, const void *image_dev, int image_dtyp
                    az_stream_t stream);
 
 /*
+ * az_integrate1d / az_integrate2d (by the integrator's kind) without any device allocation
+ * by the call.  The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc while they run -- for instance a plugin inside a host program whose own
+ * memory pool has reserved the device memory, or an acquisition loop that forbids
+ * allocations (which can block and synchronise the device) once set-up is over.  The
+ * integrator itself must have been built beforehand.
+ *
+ * The partial sums the forward keeps between its two kernels go to one fixed array of
+ * AZ_NOALLOC_SCRATCH_BYTES compiled into this library; every GPU that loads the library holds
+ * that memory until the process exits.  A call needs 3 * segments * 8 bytes (FP64) or
+ * 3 * segments * 4 bytes (FP32 compensated), segments = az_info.n_segments; a larger need is
+ * refused with AZ_ESHAPE and a message giving both sizes.  Nothing in the array has to start
+ * at zero: each call writes every partial sum it later reads.
+ *
+ * All calls on a device share the array and it keeps the last call's contents, so calls
+ * that overlap on the GPU (different streams, or host threads without ordering) race and
+ * give wrong results: order them on one stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Arguments, outputs and errors are otherwise those of
+ * az_integrate1d.
+ */
+#define AZ_NOALLOC_SCRATCH_BYTES (8u << 20)
+int az_integrate_noalloc(const az_integrator *h, const void *image_dev, int image_dtype,
+                         const float *dark, const float *flat, const float *solid_angle,
+                         const float *polarization, int precision, void *out_I,
+                         void *out_sum_signal, void *out_sum_norm, void *out_count,
+                         az_stream_t stream);
+
+/*
  * Many frames through one matrix ("several detectors / frames", Sec. 5.2.2 end): frames
  * device [n_frames][ny][nx]; the frame-independent sums N and C are formed once per call
  * and each matrix entry is applied to frames_per_pass frames per read.  FP32 compensated.

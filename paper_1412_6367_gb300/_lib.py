@@ -70,6 +70,7 @@ SIGNATURES = {
     "az_integrator_destroy": ([vp], None),
     "az_integrate1d": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "az_integrate2d": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
+    "az_integrate_noalloc": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "az_integrate_batch": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_batch_host": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_backward": ([vp, vp, vp, vp, vp, vp, i32, vp, vp, vp], i32),

@@ -234,6 +234,26 @@ class Integrator:
             out = Result(*(t.view(shp) for t in out))
         return out
 
+    def integrate_noalloc(self, image, dark=None, flat=None, solid_angle=None, polarization=None,
+                          precision="fp32", out=None) -> Result:
+        """One frame like integrate(), through az_integrate_noalloc: the call allocates no
+        device memory itself (its partial sums use a fixed array inside the library).  Pass
+        preallocated `out` tensors to keep the whole call free of allocation."""
+        prec = _code(PRECISIONS, precision, "precision")
+        npix = self.info["ny"] * self.info["nx"]
+        img = _dev(image, "image", numel=npix)
+        dt = torch.float64 if prec == L.PREC_FP64 else torch.float32
+        if out is None:
+            out = Result(*(torch.empty(self.nrows, dtype=dt, device=image.device) for _ in range(4)))
+        check(self._lib.az_integrate_noalloc(
+            self._h, img, image_dtype_code(image), *self._corr(dark, flat, solid_angle, polarization),
+            prec, _dev(out.I, "I", dt), _dev(out.sum_signal, "S", dt),
+            _dev(out.sum_norm, "N", dt), _dev(out.count, "C", dt), _stream(image.device)))
+        if self.info["npt_azim"]:
+            shp = (self.info["npt_azim"], self.info["npt_rad"])
+            out = Result(*(t.view(shp) for t in out))
+        return out
+
     def integrate_batch(self, frames, dark=None, flat=None, solid_angle=None, polarization=None,
                         out=None):
         """Many frames [n, ny, nx] through the matrix (az_integrate_batch, FP32 compensated).

@@ -179,6 +179,9 @@ int stable_sort_pairs(uint32_t *keys, int32_t *vals, int64_t n, int key_bits, cu
 int forward_single(const az_integrator *h, const void *image, int dtype, const float *dark,
                    const float *flat, const float *sa, const float *pol, int precision,
                    void *oI, void *oS, void *oN, void *oC, cudaStream_t s);
+int forward_single_into(const az_integrator *h, const void *image, int dtype, const float *dark,
+                        const float *flat, const float *sa, const float *pol, int precision,
+                        void *oI, void *oS, void *oN, void *oC, void *partial, cudaStream_t s);
 int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
                   const float *flat, const float *sa, const float *pol, float *oI, float *oS,
                   float *oN, float *oC, cudaStream_t s);

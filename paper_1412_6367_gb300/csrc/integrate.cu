@@ -945,6 +945,33 @@ int forward_single(const az_integrator *h, const void *image, int dtype, const f
     return AZ_OK;
 }
 
+// forward_single with the per-segment partial sums in a buffer the caller supplies (at least
+// 3 * nseg values of the accumulation type) instead of the integrator's own; no profiling.
+int forward_single_into(const az_integrator *h, const void *image, int dtype, const float *dark,
+                        const float *flat, const float *sa, const float *pol, int precision,
+                        void *oI, void *oS, void *oN, void *oC, void *partial, cudaStream_t s) {
+    const bool fp64 = precision == AZ_PREC_FP64;
+    Inst d = make_inst(h, fp64);
+    d.partial = partial;
+    d.img = static_cast<const char *>(image);
+    d.dark = dark; d.flat = flat; d.sa = sa; d.pol = pol;
+    d.oI = oI; d.oS = oS; d.oN = oN; d.oC = oC;
+    const int planes = 1 + (dark != nullptr) + (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
+    StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries,
+                                fp64 ? 8 : 4, rec_words_of(h), d.stage_entries);
+    const int eng = engine_for(h);
+    TmaSet tm;
+    AZ_TRY(make_maps(h, eng, image, h->ny, dark, flat, sa, pol, tm));
+    if (fp64) {
+        AZ_TRY((run_phase1_dt<double, double, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s)));
+        AZ_TRY((run_phase2<double, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s)));
+    } else {
+        AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s)));
+        AZ_TRY((run_phase2<float, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s)));
+    }
+    return AZ_OK;
+}
+
 int batch_norm(az_integrator *h, const float *flat, const float *sa, const float *pol, float *oN,
                float *oC, cudaStream_t s) {
     Inst d = make_inst(h, false);
