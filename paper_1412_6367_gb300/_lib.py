@@ -41,10 +41,10 @@ class Info(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 4), ("total_ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("total_ms", ctypes.c_double * 5)]
 
 
-PROFILE_KINDS = ("phase1_frames", "phase1_norm", "phase1_single", "phase2_finalize")
+PROFILE_KINDS = ("phase1_frames", "phase1_norm", "phase1_single", "phase2_finalize", "dark_gather")
 
 _lock = threading.Lock()
 _lib = None

@@ -998,6 +998,7 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
         if (L.ent_dark.bytes < sizeof(float) * (size_t)L.padded_nnz)
             AZ_TRY(L.ent_dark.alloc(sizeof(float) * (size_t)L.padded_nnz));
         const int64_t blocks = std::min<int64_t>((L.padded_nnz + 255) / 256, (int64_t)num_sms() * 8);
+        ProfScope ps(&h->prof, 4, s);
         gather_dark_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
             L.ent_pix.as<int32_t>(), dark, L.padded_nnz, L.ent_dark.as<float>());
         AZ_CUDA(cudaGetLastError());
