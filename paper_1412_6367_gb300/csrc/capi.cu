@@ -39,13 +39,13 @@ int alloc_scratch(az_integrator *h) {
 
 int finish_build(az_integrator *h, cudaStream_t s) {
     // defaults measured on the Pilatus-6M workload; az_autotune refines them per matrix
-    int th = 16, tw = 64;
+    int th = 8, tw = 224;
     if (build_tiled_layout(h, th, tw, s) != AZ_OK) {  // a denser matrix: smaller tiles
         th = 8;
-        tw = 32;
+        tw = 64;
         AZ_TRY(build_tiled_layout(h, th, tw, s));
     }
-    h->frames_per_pass = 16;
+    h->frames_per_pass = 8;
     h->rows_per_warp = 32 / h->frames_per_pass;
     AZ_TRY(alloc_scratch(h));
     AZ_TRY(h->status.alloc(sizeof(int)));
@@ -489,12 +489,12 @@ extern "C" int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t str
     cudaEvent_t e0, e1;
     AZ_CUDA(cudaEventCreate(&e0));
     AZ_CUDA(cudaEventCreate(&e1));
-    const int tiles[][2] = {{16, 128}, {16, 64}, {8, 256}, {8, 128}, {32, 64}, {32, 128}, {8, 64}};
-    const int fpps[] = {4, 8, 16, 32};
+    const int tiles[][2] = {{8, 224}, {8, 192}, {16, 64}, {16, 96}, {8, 128}, {16, 128}, {32, 64}, {8, 64}};
+    const int fpps[] = {4, 8, 16};
     const int engines[] = {AZ_COPY_TMA, AZ_COPY_ASYNC};
     double best = 1e30;
     int bt = -1, bf = h->frames_per_pass, be = h->copy_engine;
-    const int tile_count = 7;
+    const int tile_count = (int)(sizeof(tiles) / sizeof(tiles[0]));
     for (int ti = 0; ti < tile_count; ++ti) {
         if (build_tiled_layout(h, tiles[ti][0], tiles[ti][1], s) != AZ_OK) { clear_error(); continue; }
         AZ_TRY(alloc_scratch(h));

@@ -144,7 +144,7 @@ struct az_integrator {
     azint::DevBuf csc_ptr, csc_row, csc_w64, csc_w32;
     azint::TiledLayout tl;
     // tuning
-    int rows_per_warp = 2, frames_per_pass = 16, copy_engine = AZ_COPY_TMA;
+    int rows_per_warp = 4, frames_per_pass = 8, copy_engine = AZ_COPY_TMA;
     // scratch: per-segment partial sums and per-row frame-independent sums
     azint::DevBuf partial;     // float or double [planes][nseg]
     size_t partial_bytes = 0;
@@ -258,13 +258,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 // Kahan-compensated FP32 accumulation (Sec. 5.2.2): the running sum s and the compensation
 // c (value = s - c).  The product is fused into the first subtraction (one rounding).
+// Kahan accumulator with the compensation kept negated (nc = -c), so that one step is a
+// fused multiply-add and three additions: y = w v + nc, t = s + y, nc = y - (t - s), s = t.
 struct Kahan {
-    float s, c;
+    float s, nc;
 };
 __device__ __forceinline__ void kahan_add(Kahan &k, float w, float v) {
-    float y = __fmaf_rn(w, v, -k.c);
+    float y = __fmaf_rn(w, v, k.nc);
     float t = __fadd_rn(k.s, y);
-    k.c = __fsub_rn(__fsub_rn(t, k.s), y);
+    k.nc = __fsub_rn(y, __fsub_rn(t, k.s));
     k.s = t;
 }
 // Merge b into a with an error-free TwoSum of the running sums.
@@ -272,15 +274,15 @@ __device__ __forceinline__ void kahan_merge(Kahan &a, const Kahan &b) {
     float t = __fadd_rn(a.s, b.s);
     float z = __fsub_rn(t, a.s);
     float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, z)), __fsub_rn(b.s, z));
-    a.c = __fsub_rn(__fadd_rn(a.c, b.c), e);
+    a.nc = __fadd_rn(__fadd_rn(a.nc, b.nc), e);
     a.s = t;
 }
-__device__ __forceinline__ float kahan_value(const Kahan &k) { return __fsub_rn(k.s, k.c); }
+__device__ __forceinline__ float kahan_value(const Kahan &k) { return __fadd_rn(k.s, k.nc); }
 
 __device__ __forceinline__ Kahan shfl_xor(const Kahan &k, int m) {
     Kahan r;
     r.s = __shfl_xor_sync(0xffffffffu, k.s, m);
-    r.c = __shfl_xor_sync(0xffffffffu, k.c, m);
+    r.nc = __shfl_xor_sync(0xffffffffu, k.nc, m);
     return r;
 }
 #endif

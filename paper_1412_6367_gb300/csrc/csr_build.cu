@@ -659,11 +659,82 @@ __global__ void tile_keys_kernel(TileGeom T, const int32_t *__restrict__ idx, in
         key[k] = (uint32_t)tile_of(T, idx[k]);
 }
 
-__global__ void pad8_kernel(const int32_t *in, int32_t *out, int64_t n) {
+// Per segment (flagged first entry e, segment id s): first entry, row and tile.
+__global__ void seg_info_kernel(const int32_t *__restrict__ flag, const int32_t *__restrict__ segid,
+                                const int32_t *__restrict__ perm, const int32_t *__restrict__ csr_row,
+                                const uint32_t *__restrict__ tkey, int64_t n,
+                                int32_t *__restrict__ first, int32_t *__restrict__ row,
+                                int32_t *__restrict__ tile) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[e]) continue;
+        const int32_t s = segid[e];
+        first[s] = (int32_t)e;
+        row[s] = csr_row[perm[e]];
+        tile[s] = (int32_t)tkey[e];
+    }
+}
+
+// Segment lengths rounded up to whole quads of entries.
+__global__ void quad_len_kernel(const int32_t *__restrict__ len, int64_t n, int32_t *__restrict__ plen) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
-        out[k] = (in[k] + 7) & ~7;
+        plen[k] = (len[k] + 3) & ~3;
 }
+
+// Padded entries of a tile: its segments' quad-rounded lengths, rounded up to 8.
+__global__ void tile_pad_kernel(const int32_t *__restrict__ tile_seg_ptr, const int32_t *__restrict__ pstart,
+                                int ntiles, int32_t *__restrict__ tpad) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+         t += (int64_t)gridDim.x * blockDim.x)
+        tpad[t] = (pstart[tile_seg_ptr[t + 1]] - pstart[tile_seg_ptr[t]] + 7) & ~7;
+}
+
+// Padded start and end of every segment.
+__global__ void seg_span_kernel(const int32_t *__restrict__ seg_tile, const int32_t *__restrict__ pstart,
+                                const int32_t *__restrict__ plen, const int32_t *__restrict__ tile_seg_ptr,
+                                const int32_t *__restrict__ tile_ent_ptr, int nseg,
+                                int32_t *__restrict__ start, int32_t *__restrict__ end) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int t = seg_tile[s];
+        const int32_t a = tile_ent_ptr[t] + pstart[s] - pstart[tile_seg_ptr[t]];
+        start[s] = a;
+        end[s] = a + plen[s];
+    }
+}
+
+__global__ void fill_u16_kernel(uint16_t *__restrict__ out, int64_t n, uint16_t v) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        out[k] = v;
+}
+
+// Tile key of each entry of a permuted entry list.
+__global__ void tile_keys_perm_kernel(TileGeom T, const int32_t *__restrict__ idx,
+                                      const int32_t *__restrict__ perm, int64_t n,
+                                      uint32_t *__restrict__ key) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        key[k] = (uint32_t)tile_of(T, idx[perm[k]]);
+}
+
+// Segment of each entry from the segment-start flags and their exclusive scan.
+__global__ void seg_index_kernel(const int32_t *__restrict__ flag, const int32_t *__restrict__ segid,
+                                 int64_t n, int32_t *__restrict__ seg) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        seg[e] = segid[e] - 1 + flag[e];
+}
+
+// Sort key putting the longer segments of a tile first: max_len - length of the segment.
+__global__ void seg_len_key_kernel(const int32_t *__restrict__ seg, const int32_t *__restrict__ len,
+                                   int32_t max_len, int64_t n, uint32_t *__restrict__ key) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        key[e] = (uint32_t)(max_len - len[seg[e]]);
+}
+
 
 __global__ void seg_flags_kernel(const uint32_t *__restrict__ tkey, const int32_t *__restrict__ perm,
                                  const int32_t *__restrict__ csr_row, int64_t n,
@@ -678,52 +749,28 @@ __global__ void seg_flags_kernel(const uint32_t *__restrict__ tkey, const int32_
 
 struct TiledFillArgs {
     TileGeom T;
-    const uint32_t *tkey;
-    const int32_t *perm, *csr_row, *csr_idx;
+    const int32_t *perm, *csr_idx;
     const double *csr_w;
-    const int32_t *flag, *seg_id, *tile_unp, *tile_pad;
+    const int32_t *segx, *seg_first, *seg_start;
     uint16_t *loc;
     int32_t *pix;
     float *w32;
     double *w64;
-    int32_t *seg_start, *seg_row, *seg_tile;
     int64_t n;
 };
 
 __global__ void tiled_fill_kernel(TiledFillArgs A) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < A.n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)A.tkey[e];
+        const int32_t s = A.segx[e];
+        const int64_t pe = (int64_t)A.seg_start[s] + (e - A.seg_first[s]);
         const int32_t k = A.perm[e];
-        const int64_t pe = (int64_t)A.tile_pad[t] + (e - A.tile_unp[t]);
         const int32_t p = A.csr_idx[k];
         A.loc[pe] = (uint16_t)tile_loc(A.T, p);
         const double w = A.csr_w[k];
         A.w64[pe] = w;
         A.w32[pe] = (float)w;
         A.pix[pe] = p;
-        if (A.flag[e]) {
-            const int32_t s = A.seg_id[e];
-            A.seg_start[s] = (int32_t)pe;
-            A.seg_row[s] = A.csr_row[k];
-            A.seg_tile[s] = t;
-        }
-    }
-}
-
-// Segment ends: the next segment of the same tile, or the tile's last real entry.
-__global__ void seg_end_kernel(const int32_t *__restrict__ seg_start,
-                               const int32_t *__restrict__ seg_tile,
-                               const int32_t *__restrict__ tile_pad,
-                               const int32_t *__restrict__ tile_cnt, int nseg,
-                               int32_t *__restrict__ seg_end) {
-    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nseg;
-         s += (int64_t)gridDim.x * blockDim.x) {
-        const int t = seg_tile[s];
-        if (s + 1 < nseg && seg_tile[s + 1] == t)
-            seg_end[s] = seg_start[s + 1];
-        else
-            seg_end[s] = tile_pad[t] + tile_cnt[t];
     }
 }
 
@@ -954,7 +1001,7 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     T.ntx = (h->nx + tw - 1) / tw;
     const int nty = (h->ny + th - 1) / th;
     const int ntiles = T.ntx * nty;
-    if ((int64_t)4 * T.ss > 65535) return fail(AZ_EINVAL, "tile %dx%d too large", th, tw);
+    if ((int64_t)4 * T.ss + 32 > 65535) return fail(AZ_EINVAL, "tile %dx%d too large", th, tw);
 
     // row of each CSR entry, tile key of each CSR entry, stable sort by tile
     DevBuf csr_row, tkey, perm;
@@ -966,35 +1013,47 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_TRY(launch_gs(tile_keys_kernel, nnz, s, T, h->csr_idx.as<int32_t>(), nnz, tkey.as<uint32_t>()));
     AZ_TRY(launch_gs(iota_kernel, nnz, s, perm.as<int32_t>(), nnz));
     AZ_TRY(stable_sort_pairs(tkey.as<uint32_t>(), perm.as<int32_t>(), nnz, bits_for(ntiles - 1), s));
-
-    // entries per tile, padded starts (multiples of 8 entries), unpadded starts
-    DevBuf tcnt, tpadcnt, tunp;
-    L.tile_ent_ptr.release();
-    AZ_TRY(tcnt.alloc(sizeof(int32_t) * ntiles));
-    AZ_TRY(tpadcnt.alloc(sizeof(int32_t) * ntiles));
-    AZ_TRY(tunp.alloc(sizeof(int32_t) * (ntiles + 1)));
-    AZ_TRY(L.tile_ent_ptr.alloc(sizeof(int32_t) * (ntiles + 1)));
-    AZ_CUDA(cudaMemsetAsync(tcnt.p, 0, sizeof(int32_t) * ntiles, s));
     {
-        // count entries per tile from the sorted keys
-        DevBuf tk32;
-        AZ_TRY(tk32.alloc(sizeof(int32_t) * nnz));
-        AZ_CUDA(cudaMemcpyAsync(tk32.p, tkey.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, s));
-        AZ_TRY(launch_gs(count_keys_kernel, nnz, s, tk32.as<int32_t>(), nnz, tcnt.as<int32_t>()));
+        // Within a tile, order the segments (runs of one row) by decreasing length, rows in
+        // increasing order among equal lengths; the entries of a segment keep pixel order.
+        // Warps that take consecutive segments then get runs of similar length.
+        DevBuf f0, id0, seg0, len0, mx0, key2;
+        AZ_TRY(f0.alloc(sizeof(int32_t) * nnz));
+        AZ_TRY(id0.alloc(sizeof(int32_t) * (nnz + 1)));
+        AZ_TRY(seg0.alloc(sizeof(int32_t) * nnz));
+        AZ_TRY(launch_gs(seg_flags_kernel, nnz, s, tkey.as<uint32_t>(), perm.as<int32_t>(),
+                         csr_row.as<int32_t>(), nnz, f0.as<int32_t>()));
+        AZ_TRY(exclusive_scan_i32(f0.as<int32_t>(), id0.as<int32_t>(), nnz, s));
+        int32_t nseg0 = 0;
+        AZ_CUDA(cudaMemcpyAsync(&nseg0, id0.as<int32_t>() + nnz, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         AZ_CUDA(cudaStreamSynchronize(s));
+        AZ_TRY(launch_gs(seg_index_kernel, nnz, s, f0.as<int32_t>(), id0.as<int32_t>(), nnz,
+                         seg0.as<int32_t>()));
+        AZ_TRY(len0.alloc(sizeof(int32_t) * std::max(nseg0, 1)));
+        AZ_CUDA(cudaMemsetAsync(len0.p, 0, sizeof(int32_t) * std::max(nseg0, 1), s));
+        AZ_TRY(launch_gs(count_keys_kernel, nnz, s, seg0.as<int32_t>(), nnz, len0.as<int32_t>()));
+        AZ_TRY(mx0.alloc(sizeof(int32_t)));
+        max_kernel<<<1, 1024, 0, s>>>(len0.as<int32_t>(), nseg0, mx0.as<int32_t>());
+        AZ_CUDA(cudaGetLastError());
+        int32_t max_len = 0;
+        AZ_CUDA(cudaMemcpyAsync(&max_len, mx0.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        AZ_CUDA(cudaStreamSynchronize(s));
+        AZ_TRY(key2.alloc(sizeof(uint32_t) * nnz));
+        AZ_TRY(launch_gs(seg_len_key_kernel, nnz, s, seg0.as<int32_t>(), len0.as<int32_t>(), max_len,
+                         nnz, key2.as<uint32_t>()));
+        AZ_TRY(stable_sort_pairs(key2.as<uint32_t>(), perm.as<int32_t>(), nnz, bits_for(max_len), s));
+        AZ_TRY(launch_gs(tile_keys_perm_kernel, nnz, s, T, h->csr_idx.as<int32_t>(), perm.as<int32_t>(),
+                         nnz, tkey.as<uint32_t>()));
+        AZ_TRY(stable_sort_pairs(tkey.as<uint32_t>(), perm.as<int32_t>(), nnz, bits_for(ntiles - 1), s));
     }
-    AZ_TRY(launch_gs(pad8_kernel, ntiles, s, tcnt.as<int32_t>(), tpadcnt.as<int32_t>(), (int64_t)ntiles));
-    AZ_TRY(exclusive_scan_i32(tpadcnt.as<int32_t>(), L.tile_ent_ptr.as<int32_t>(), ntiles, s));
-    AZ_TRY(exclusive_scan_i32(tcnt.as<int32_t>(), tunp.as<int32_t>(), ntiles, s));
-    int32_t padded = 0;
-    AZ_CUDA(cudaMemcpyAsync(&padded, L.tile_ent_ptr.as<int32_t>() + ntiles, sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, s));
-    AZ_CUDA(cudaStreamSynchronize(s));
 
-    // segment flags and ids
-    DevBuf flag, segid;
+    // Segments (runs of one row inside a tile) in the final entry order.  Each segment is
+    // padded to whole quads of entries with dummy entries of weight 0 whose location is the
+    // zero band after every staged plane (pixel -1), so that reductions read whole quads only.
+    DevBuf flag, segid, segx;
     AZ_TRY(flag.alloc(sizeof(int32_t) * nnz));
     AZ_TRY(segid.alloc(sizeof(int32_t) * (nnz + 1)));
+    AZ_TRY(segx.alloc(sizeof(int32_t) * nnz));
     AZ_TRY(launch_gs(seg_flags_kernel, nnz, s, tkey.as<uint32_t>(), perm.as<int32_t>(),
                      csr_row.as<int32_t>(), nnz, flag.as<int32_t>()));
     AZ_TRY(exclusive_scan_i32(flag.as<int32_t>(), segid.as<int32_t>(), nnz, s));
@@ -1002,43 +1061,64 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_CUDA(cudaMemcpyAsync(&nseg, segid.as<int32_t>() + nnz, sizeof(int32_t),
                             cudaMemcpyDeviceToHost, s));
     AZ_CUDA(cudaStreamSynchronize(s));
+    AZ_TRY(launch_gs(seg_index_kernel, nnz, s, flag.as<int32_t>(), segid.as<int32_t>(), nnz,
+                     segx.as<int32_t>()));
+    DevBuf seg_first, seg_row, seg_tile, seg_len, seg_plen, pstart;
+    AZ_TRY(seg_first.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(seg_row.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(seg_tile.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(seg_len.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(seg_plen.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(pstart.alloc(sizeof(int32_t) * (nseg + 1)));
+    AZ_TRY(launch_gs(seg_info_kernel, nnz, s, flag.as<int32_t>(), segid.as<int32_t>(), perm.as<int32_t>(),
+                     csr_row.as<int32_t>(), tkey.as<uint32_t>(), nnz, seg_first.as<int32_t>(),
+                     seg_row.as<int32_t>(), seg_tile.as<int32_t>()));
+    AZ_CUDA(cudaMemsetAsync(seg_len.p, 0, sizeof(int32_t) * nseg, s));
+    AZ_TRY(launch_gs(count_keys_kernel, nnz, s, segx.as<int32_t>(), nnz, seg_len.as<int32_t>()));
+    AZ_TRY(launch_gs(quad_len_kernel, nseg, s, seg_len.as<int32_t>(), (int64_t)nseg, seg_plen.as<int32_t>()));
+    AZ_TRY(exclusive_scan_i32(seg_plen.as<int32_t>(), pstart.as<int32_t>(), nseg, s));
 
-    // padded entry arrays and segment starts
+    // segments per tile -> tile_seg_ptr; padded entries per tile (multiple of 8) -> tile_ent_ptr
+    DevBuf scnt, tpadcnt;
+    AZ_TRY(scnt.alloc(sizeof(int32_t) * ntiles));
+    AZ_TRY(tpadcnt.alloc(sizeof(int32_t) * ntiles));
+    AZ_CUDA(cudaMemsetAsync(scnt.p, 0, sizeof(int32_t) * ntiles, s));
+    AZ_TRY(launch_gs(count_keys_kernel, nseg, s, seg_tile.as<int32_t>(), (int64_t)nseg, scnt.as<int32_t>()));
+    AZ_TRY(L.tile_seg_ptr.alloc(sizeof(int32_t) * (ntiles + 1)));
+    AZ_TRY(exclusive_scan_i32(scnt.as<int32_t>(), L.tile_seg_ptr.as<int32_t>(), ntiles, s));
+    AZ_TRY(launch_gs(tile_pad_kernel, ntiles, s, L.tile_seg_ptr.as<int32_t>(), pstart.as<int32_t>(), ntiles,
+                     tpadcnt.as<int32_t>()));
+    L.tile_ent_ptr.release();
+    AZ_TRY(L.tile_ent_ptr.alloc(sizeof(int32_t) * (ntiles + 1)));
+    AZ_TRY(exclusive_scan_i32(tpadcnt.as<int32_t>(), L.tile_ent_ptr.as<int32_t>(), ntiles, s));
+    int32_t padded = 0;
+    AZ_CUDA(cudaMemcpyAsync(&padded, L.tile_ent_ptr.as<int32_t>() + ntiles, sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, s));
+    AZ_CUDA(cudaStreamSynchronize(s));
+
+    // padded entry arrays
     L.ent_loc.release(); L.ent_w32.release(); L.ent_w64.release();
     AZ_TRY(L.ent_loc.alloc(sizeof(uint16_t) * (size_t)padded));
     AZ_TRY(L.ent_w32.alloc(sizeof(float) * (size_t)padded));
     AZ_TRY(L.ent_w64.alloc(sizeof(double) * (size_t)padded));
     AZ_TRY(L.ent_pix.alloc(sizeof(int32_t) * (size_t)padded));
     L.ent_dark.release();
-    AZ_CUDA(cudaMemsetAsync(L.ent_loc.p, 0, L.ent_loc.bytes, s));
+    AZ_TRY(launch_gs(fill_u16_kernel, padded, s, L.ent_loc.as<uint16_t>(), (int64_t)padded,
+                     (uint16_t)(4 * T.ss)));  // dummies read the zero band
     AZ_CUDA(cudaMemsetAsync(L.ent_w32.p, 0, L.ent_w32.bytes, s));
     AZ_CUDA(cudaMemsetAsync(L.ent_w64.p, 0, L.ent_w64.bytes, s));
     AZ_CUDA(cudaMemsetAsync(L.ent_pix.p, 0xff, L.ent_pix.bytes, s));  // padding entries: -1
-    DevBuf seg_row, seg_tile;
     AZ_TRY(L.seg_ent_ptr.alloc(sizeof(int32_t) * 2 * (size_t)nseg));  // [start | end]
-    AZ_TRY(seg_row.alloc(sizeof(int32_t) * nseg));
-    AZ_TRY(seg_tile.alloc(sizeof(int32_t) * nseg));
+    AZ_TRY(launch_gs(seg_span_kernel, nseg, s, seg_tile.as<int32_t>(), pstart.as<int32_t>(),
+                     seg_plen.as<int32_t>(), L.tile_seg_ptr.as<int32_t>(), L.tile_ent_ptr.as<int32_t>(),
+                     nseg, L.seg_ent_ptr.as<int32_t>(), L.seg_ent_ptr.as<int32_t>() + nseg));
     TiledFillArgs A;
-    A.T = T; A.tkey = tkey.as<uint32_t>(); A.perm = perm.as<int32_t>();
-    A.csr_row = csr_row.as<int32_t>(); A.csr_idx = h->csr_idx.as<int32_t>();
-    A.csr_w = h->csr_w64.as<double>(); A.flag = flag.as<int32_t>(); A.seg_id = segid.as<int32_t>();
-    A.tile_unp = tunp.as<int32_t>(); A.tile_pad = L.tile_ent_ptr.as<int32_t>();
+    A.T = T; A.perm = perm.as<int32_t>(); A.csr_idx = h->csr_idx.as<int32_t>();
+    A.csr_w = h->csr_w64.as<double>(); A.segx = segx.as<int32_t>();
+    A.seg_first = seg_first.as<int32_t>(); A.seg_start = L.seg_ent_ptr.as<int32_t>();
     A.loc = L.ent_loc.as<uint16_t>(); A.w32 = L.ent_w32.as<float>(); A.w64 = L.ent_w64.as<double>();
-    A.pix = L.ent_pix.as<int32_t>();
-    A.seg_start = L.seg_ent_ptr.as<int32_t>(); A.seg_row = seg_row.as<int32_t>();
-    A.seg_tile = seg_tile.as<int32_t>(); A.n = nnz;
+    A.pix = L.ent_pix.as<int32_t>(); A.n = nnz;
     AZ_TRY(launch_gs(tiled_fill_kernel, nnz, s, A));
-    AZ_TRY(launch_gs(seg_end_kernel, nseg, s, L.seg_ent_ptr.as<int32_t>(), seg_tile.as<int32_t>(),
-                     L.tile_ent_ptr.as<int32_t>(), tcnt.as<int32_t>(), nseg,
-                     L.seg_ent_ptr.as<int32_t>() + nseg));
-
-    // segments per tile -> tile_seg_ptr
-    DevBuf scnt;
-    AZ_TRY(scnt.alloc(sizeof(int32_t) * ntiles));
-    AZ_CUDA(cudaMemsetAsync(scnt.p, 0, sizeof(int32_t) * ntiles, s));
-    AZ_TRY(launch_gs(count_keys_kernel, nseg, s, seg_tile.as<int32_t>(), (int64_t)nseg, scnt.as<int32_t>()));
-    AZ_TRY(L.tile_seg_ptr.alloc(sizeof(int32_t) * (ntiles + 1)));
-    AZ_TRY(exclusive_scan_i32(scnt.as<int32_t>(), L.tile_seg_ptr.as<int32_t>(), ntiles, s));
 
     // slots: segments in row order (stable sort of segment ids by row)
     DevBuf skey, sperm, rcnt;
@@ -1060,7 +1140,7 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_TRY(aflag.alloc(sizeof(int32_t) * ntiles));
     AZ_TRY(apos.alloc(sizeof(int32_t) * (ntiles + 1)));
     AZ_TRY(mx.alloc(sizeof(int32_t) * 2));
-    AZ_TRY(launch_gs(active_flags_kernel, ntiles, s, tcnt.as<int32_t>(), ntiles, aflag.as<int32_t>()));
+    AZ_TRY(launch_gs(active_flags_kernel, ntiles, s, scnt.as<int32_t>(), ntiles, aflag.as<int32_t>()));
     AZ_TRY(exclusive_scan_i32(aflag.as<int32_t>(), apos.as<int32_t>(), ntiles, s));
     int32_t n_active = 0;
     AZ_CUDA(cudaMemcpyAsync(&n_active, apos.as<int32_t>() + ntiles, sizeof(int32_t),

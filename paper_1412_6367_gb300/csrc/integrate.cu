@@ -121,10 +121,23 @@ __device__ __forceinline__ TileDesc load_desc(const Inst &d, int64_t local) {
     return TileDesc{x.x, x.y, x.z, x.w, y.x, y.y};
 }
 
-// Words between two staged planes: four 128-byte aligned row-class slots.  (Planes are
-// spread over the shared-memory banks by a per-plane shift of 4 * (plane mod 4) words that
-// the copies apply, see produce().)
-__host__ __device__ __forceinline__ uint32_t plane_stride(int ss) { return 4u * (uint32_t)ss; }
+// Words between two staged planes: four 128-byte aligned row-class slots and a band of 32
+// words that holds zeros (the padding entries of the matrix point there: their weight is 0
+// and the value they read is 0, whatever the image holds).  Planes are spread over the
+// shared-memory banks by per-plane shifts of 4 * s words that the copies apply.
+constexpr uint32_t kZeroBand = 32;
+__host__ __device__ __forceinline__ uint32_t plane_stride(int ss) { return 4u * (uint32_t)ss + kZeroBand; }
+
+// Zero the band after every plane of every stage (never written by the copies).
+__device__ __forceinline__ void zero_bands(unsigned char *first_plane, uint32_t stage_bytes, int nstages,
+                                           int planes, uint32_t pw) {
+    const int per_stage = planes * (int)kZeroBand;
+    for (int i = threadIdx.x; i < nstages * per_stage; i += blockDim.x) {
+        const int st = i / per_stage, r = i - st * per_stage;
+        const int pl = r / (int)kZeroBand, w = r - pl * (int)kZeroBand;
+        reinterpret_cast<uint32_t *>(first_plane + (size_t)st * stage_bytes)[(size_t)pl * pw + pw - kZeroBand + w] = 0u;
+    }
+}
 
 // Four 2D tensor maps per staged array, one per tile-row class (rows of equal index mod 4,
 // 16 * nx bytes apart).  Index: 0 image, 1 dark, 2 flat, 3 solid angle, 4 polarisation.
@@ -297,6 +310,12 @@ __device__ void produce(const Inst &d, const TmaSet &tm, int64_t local, const Ti
     } else {
         mbar_arrive(bar);
     }
+    if (pwarp == 0) {
+        // the zero band of every plane of this item (planes of different instances have
+        // different strides, so the bands move from item to item)
+        for (int pl = 0; pl < np; ++pl) planes[(size_t)pl * pw + pw - kZeroBand + lane] = 0u;
+        __syncwarp();
+    }
     if (pwarp == 0 && lane == 0) {
         int *h = reinterpret_cast<int *>(stage);
         h[0] = td.ns; h[1] = group; h[2] = nimg; h[3] = h[4] = h[5] = h[6] = -1;
@@ -333,7 +352,7 @@ __device__ __forceinline__ double img_f64(uint32_t w) {
 template <class A> struct Acc;
 template <> struct Acc<float> {
     Kahan k;
-    __device__ void zero() { k.s = 0.f; k.c = 0.f; }
+    __device__ void zero() { k.s = 0.f; k.nc = 0.f; }
     __device__ void add(float w, float v) { kahan_add(k, w, v); }
     __device__ void merge(const Acc<float> &o) { kahan_merge(k, o.k); }
     __device__ void merge_xor(int m) {
@@ -392,9 +411,10 @@ template <> struct W4<double> {
 //   frames pass: quantity q = frame q of the item, value = cast(image) - dark;
 //   norm pass:   q = 0: flat * solid angle * polarisation, q = 1: 1 (the count);
 //   single pass: q = 0: cast(image) - dark, q = 1: the normalisation, q = 2: 1, q = 3 idle.
-// Entries are read four at a time from 4-aligned positions (one 8-byte read of the locations,
-// 16-byte reads of the weights and per-entry darks); entry e goes to accumulator e mod 4 and
-// the four are combined as ((a0 + a1) + (a2 + a3)).  Every quantity of every pass is reduced
+// Segments start on a multiple of 4 entries and hold whole quads (the layout pads them with
+// entries of weight 0 that read the plane's zero band).  Entries are read four at a time (one
+// 8-byte read of the locations, 16-byte reads of the weights and per-entry darks); entry e
+// goes to accumulator e mod 4 and the four are combined as ((a0 + a1) + (a2 + a3)).  Every quantity of every pass is reduced
 // by this same sequence of operations, so a flat image with unit corrections gives S == N bit
 // for bit, and a frame integrated alone or in a batch gives the same bits.
 template <int Q, class AT, class WT, int MODE, int DT, bool SE>
@@ -448,7 +468,7 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
         Acc<AT> acc[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[j].zero();
-        for (int qd = e0 & ~3; qd < e1; qd += 4) {
+        for (int qd = e0; qd < e1; qd += 4) {
             const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
             const int loc[4] = {(int)(l2.x & 0xffffu), (int)(l2.x >> 16), (int)(l2.y & 0xffffu),
                                 (int)(l2.y >> 16)};
@@ -461,8 +481,6 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int e = qd + j;
-                if (e < e0 || e >= e1) continue;
                 AT x;
                 if (MODE == MODE_FRAMES) {
                     float v = img_f32<DT>(planes[oimg + loc[j]]);
@@ -598,6 +616,339 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
             consume_dispatch<AT, WT, MODE, NIMG, DT>(cp, smem + (size_t)s * sg.stage_bytes, sg, &ctr[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// frames pass with tile-resident entries
+// ------------------------------------------------------------------------------------
+// The batched frames pass spends most of its bytes on pixels, so a work item is one pixel
+// tile for every frame of the launch: the tile's record and entries (location, weight,
+// dark) are copied once into one of two entry buffers and stay there while the tile's
+// pixels stream through a ring of plane stages, G frames per stage.  One producer warp
+// issues every copy (bulk and tensor TMA); 16 consumer warps reduce.  The consumer
+// arithmetic is exactly that of the frames mode of phase1_kernel: the same entry order,
+// accumulator assignment and merge, so results do not depend on the kernel that made them.
+constexpr int kFrConsumers = 16;
+constexpr int kFrThreads = 32 * (1 + kFrConsumers);
+constexpr int kFrMaxStages = 8;
+constexpr uint32_t kFrStageHeader = 128;  // per plane stage: nimg, group, G plane offsets
+
+struct FrArgs {
+    const char *img;                      // first frame of this launch
+    int n_frames, n_groups, n_tiles;      // frames in the launch, groups of G, active tiles
+    const int32_t *tile_desc, *tile_rec;  // per active tile: descriptor [8] and record
+    const uint16_t *ent_loc;
+    const float *ent_w, *ent_dark;        // ent_dark: NULL without a dark
+    float *partial;                       // [n_frames][nseg]
+    int nseg, ny, nx, th, tw, srow, ss, ntx;
+    int *status;
+};
+
+struct FrGeom {
+    uint32_t rec_cap;       // bytes for the tile record (multiple of 128)
+    uint32_t ent_cap;       // entry capacity (multiple of 8)
+    uint32_t ebuf_bytes;    // one entry buffer (multiple of 128)
+    uint32_t plane_words;   // words per plane
+    uint32_t pstage_bytes;  // one plane stage: G planes
+    int nstages;            // plane stages
+    int dk;                 // entries carry a dark
+};
+
+__device__ __forceinline__ TileDesc fr_desc(const FrArgs &a, int item) {
+    const int4 *p = reinterpret_cast<const int4 *>(a.tile_desc) + 2 * (size_t)item;
+    const int4 x = __ldg(p), y = __ldg(p + 1);
+    return TileDesc{x.x, x.y, x.z, x.w, y.x, y.y};
+}
+
+// One thread: the tile's record, entry locations, weights and darks into entry buffer `eb`.
+__device__ __forceinline__ void fr_stage_entries(const FrArgs &a, const FrGeom &fg, const TileDesc &td,
+                                                 unsigned char *eb, uint64_t *bar) {
+    const uint32_t ne = (uint32_t)td.ne;
+    const uint32_t bytes = (uint32_t)td.rec_words * 4u + ne * (fg.dk ? 10u : 6u);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(eb, a.tile_rec + td.rec_off, (uint32_t)td.rec_words * 4u, bar);
+    if (ne) {
+        unsigned char *el = eb + fg.rec_cap;
+        unsigned char *ew = el + fg.ent_cap * 2u;
+        bulk_g2s(el, a.ent_loc + td.e_off, ne * 2u, bar);
+        bulk_g2s(ew, a.ent_w + td.e_off, ne * 4u, bar);
+        if (fg.dk) bulk_g2s(ew + fg.ent_cap * 4u, a.ent_dark + td.e_off, ne * 4u, bar);
+    }
+}
+
+// The producer warp: frames f0 .. f0 + nimg - 1 of the tile into plane stage `planes`, one
+// tensor copy per (frame, row class), as in produce(); G <= 16, so a lane has at most two
+// copies.  Frame q's box starts 4 * s_q words early, s_q = (number of earlier frames of the
+// group whose rows have the same word phase) mod 4, so that the frames of a group fall on
+// different shared-memory banks for as many frames as the phases and shifts allow.  Lane 0
+// then publishes the stage header and resets the stage's claim counter.
+template <int G>
+__device__ __forceinline__ void fr_stage_planes(const FrArgs &a, const TmaSet &tm, const TileDesc &td,
+                                                int g, uint32_t *planes, int *hdr, const FrGeom &fg,
+                                                uint64_t *bar, int *ctr) {
+    static_assert(G >= 1 && G <= 16, "a plane stage holds at most 16 frames");
+    const int lane = threadIdx.x & 31;
+    const int ti = td.t / a.ntx, tj = td.t - ti * a.ntx;
+    const int r0 = ti * a.th, c0 = tj * a.tw;
+    const int f0 = g * G;
+    const int nimg = min(G, a.n_frames - f0);
+    const int nu = a.nx & 3;
+    const int rows4 = a.th >> 2;
+    const int64_t rows_total = (int64_t)a.n_frames * a.ny;
+    const uint32_t pw = plane_stride(a.ss);
+    const int beta = (int)((reinterpret_cast<uintptr_t>(a.img) >> 2) & 3u);
+    // lane q < nimg: word phase of frame q's tile rows and its shift (earlier frames of the
+    // group with the same phase, mod 4)
+    const int64_t gl = (int64_t)(f0 + lane) * a.ny + r0;
+    const int ph = (beta + nu * (int)(gl & 3)) & 3;
+    const unsigned same = __match_any_sync(0xffffffffu, lane < nimg ? ph : 4 + lane);
+    const int sh = __popc(same & ((1u << lane) - 1u)) & 3;
+    // a lane's jobs are (frame, class) = (lane / 4, lane % 4) and (8 + lane / 4, lane % 4)
+    const int shj[2] = {__shfl_sync(0xffffffffu, sh, lane >> 2), __shfl_sync(0xffffffffu, sh, 8 + (lane >> 2))};
+    uint32_t mine = 0;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int job = lane + 32 * h2;
+        if (job >= 4 * nimg) break;
+        const int q = job >> 2, k = job & 3;
+        const int64_t g0 = (int64_t)(f0 + q) * a.ny + r0;
+        const int sl = (k - (int)(g0 & 3)) & 3;
+        if (g0 + sl < rows_total) mine += (uint32_t)(a.srow * rows4 * 4);
+    }
+    fence_proxy_async_smem();
+    if (mine)
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                     "r"(mine)
+                     : "memory");
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int job = lane + 32 * h2;
+        if (job >= 4 * nimg) break;
+        const int q = job >> 2, k = job & 3;
+        const int64_t g0 = (int64_t)(f0 + q) * a.ny + r0;
+        const int phi_row = (int)(g0 & 3);
+        const int sl = (k - phi_row) & 3;
+        if (g0 + sl >= rows_total) continue;
+        const int phi = (beta + nu * phi_row) & 3;
+        const int offk = (beta + k * nu) & 3;
+        const int cs = (nu * sl) & 3;
+        const int flag = (cs + phi - offk) >> 2;
+        const int x = c0 - 4 * (flag + shj[h2]);
+        uint32_t *dst = planes + (size_t)q * pw + (size_t)sl * a.ss;
+        const int y = (int)((g0 + sl - k) >> 2);
+        const CUtensorMap *map = &tm.m[0][k];
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+            "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+            : "memory");
+    }
+    if (lane < nimg) hdr[2 + lane] = (int)(lane * pw) + ph + 4 * sh;
+    if (lane == 0) {
+        hdr[0] = nimg;
+        hdr[1] = g;
+        *ctr = 0;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);  // publishes the header and the counter
+}
+
+// Two FP32 values in one 64-bit register, operated on by the packed f32x2 instructions
+// (round to nearest, no flush): each half gives exactly the scalar result.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 x, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// Two Kahan accumulators stepped together: the same operations as kahan_add on each half.
+__device__ __forceinline__ void kahan2_add(f32x2 &s, f32x2 &nc, f32x2 w, f32x2 v) {
+    const f32x2 y = f2_fma(w, v, nc);
+    const f32x2 t = f2_add(s, y);
+    nc = f2_sub(y, f2_sub(t, s));
+    s = t;
+}
+
+// Consumer warps: lane (sub, q) reduces segment b + sub for frame q of the stage, with the
+// entry stream of the tile's entry buffer, exactly as consume_serial does in frames mode (same
+// entry order, accumulator assignment and merge); accumulators (0, 1) and (2, 3) are stepped
+// as packed f32x2 pairs.
+template <int G, int DT, bool DK>
+__device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, const unsigned char *eb,
+                                           const uint32_t *planes, const int *hdr, int *ctr) {
+    constexpr int R = 32 / G;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane / G, q = lane % G;
+    const int *rec = reinterpret_cast<const int *>(eb);
+    const int ns = rec[1];
+    const int *slots = rec + 4;
+    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
+    const uint16_t *L = reinterpret_cast<const uint16_t *>(eb + fg.rec_cap);
+    const float *W = reinterpret_cast<const float *>(eb + fg.rec_cap + fg.ent_cap * 2u);
+    const float *D = W + fg.ent_cap;
+    const int nimg = hdr[0], g = hdr[1];
+    const bool active = q < nimg;
+    const uint32_t *P = planes + hdr[2 + (active ? q : 0)];
+    float *out = a.partial + (size_t)(g * G + q) * (size_t)a.nseg;
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, R);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        const int sl = b + sub;
+        int e0 = 0, e1 = 0, slot = 0;
+        if (sl < ns) {
+            e0 = starts[sl];
+            e1 = starts[sl + 1];
+            slot = slots[sl];
+        }
+        if (!active) e1 = e0;
+        // Segments start on a quad and hold whole quads (padding entries add w = 0 times 0).
+        f32x2 s01 = 0ull, n01 = 0ull, s23 = 0ull, n23 = 0ull;
+        for (int qd = e0; qd < e1; qd += 4) {
+            const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
+            const float4 w4 = *reinterpret_cast<const float4 *>(W + qd);
+            float v[4];
+            v[0] = img_f32<DT>(P[l2.x & 0xffffu]);
+            v[1] = img_f32<DT>(P[l2.x >> 16]);
+            v[2] = img_f32<DT>(P[l2.y & 0xffffu]);
+            v[3] = img_f32<DT>(P[l2.y >> 16]);
+            f32x2 v01 = f2_pack(v[0], v[1]), v23 = f2_pack(v[2], v[3]);
+            if (DK) {
+                const float4 d4 = *reinterpret_cast<const float4 *>(D + qd);
+                v01 = f2_sub(v01, f2_pack(d4.x, d4.y));
+                v23 = f2_sub(v23, f2_pack(d4.z, d4.w));
+            }
+            kahan2_add(s01, n01, f2_pack(w4.x, w4.y), v01);
+            kahan2_add(s23, n23, f2_pack(w4.z, w4.w), v23);
+        }
+        Kahan k[4];
+        f2_unpack(s01, k[0].s, k[1].s);
+        f2_unpack(n01, k[0].nc, k[1].nc);
+        f2_unpack(s23, k[2].s, k[3].s);
+        f2_unpack(n23, k[2].nc, k[3].nc);
+        kahan_merge(k[0], k[1]);
+        kahan_merge(k[2], k[3]);
+        kahan_merge(k[0], k[2]);
+        if (sl < ns && active) out[slot] = kahan_value(k[0]);
+    }
+}
+
+// Bounded grace wait for copies this CTA issued before giving up (every wait is bounded).
+__device__ __forceinline__ void fr_drain(uint64_t *bar, uint32_t parity) { (void)mbar_wait_bounded(bar, parity); }
+
+template <int G, int DT, bool DK>
+__global__ void __launch_bounds__(kFrThreads, 1)
+frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant__ TmaSet tm) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127u) & ~static_cast<uintptr_t>(127u));
+    const int S = fg.nstages;
+    unsigned char *ebuf0 = smem;
+    unsigned char *pst = smem + 2 * (size_t)fg.ebuf_bytes;
+    int *hdrs = reinterpret_cast<int *>(pst + (size_t)S * fg.pstage_bytes);
+    uint64_t *efull = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(hdrs) +
+                                                   (size_t)S * kFrStageHeader);
+    uint64_t *eempty = efull + 2;
+    uint64_t *pfull = eempty + 2;
+    uint64_t *pempty = pfull + S;
+    int *ctr = reinterpret_cast<int *>(pempty + S);
+    volatile int *abort_flag = ctr + S;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&efull[i], 1);
+            mbar_init(&eempty[i], kFrConsumers);
+        }
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&pfull[i], 1);
+            mbar_init(&pempty[i], kFrConsumers);
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    zero_bands(pst, fg.pstage_bytes, S, (int)(fg.pstage_bytes / (fg.plane_words * 4u)), fg.plane_words);
+    __syncthreads();
+    if (warp == 0) {
+        int k = 0, issued = 0;  // items seen, items whose entries were issued
+        uint32_t j = 0;         // plane stages issued
+        bool stop = false;
+        for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x, ++k) {
+            const TileDesc td = fr_desc(a, item);
+            const int eb = k & 1;
+            bool ok = true;
+            if (k >= 2) ok = mbar_wait_bounded(&eempty[eb], (uint32_t)(((k >> 1) - 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok || *abort_flag != 0) { stop = true; if (!ok && lane == 0) atomicExch(a.status, AZ_ETIMEOUT); break; }
+            if (lane == 0) fr_stage_entries(a, fg, td, ebuf0 + (size_t)eb * fg.ebuf_bytes, &efull[eb]);
+            issued = k + 1;
+            for (int g = 0; g < a.n_groups; ++g, ++j) {
+                const int s = (int)(j % (uint32_t)S);
+                ok = true;
+                if (j >= (uint32_t)S) ok = mbar_wait_bounded(&pempty[s], ((j / S) - 1) & 1);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok || *abort_flag != 0) { stop = true; if (!ok && lane == 0) atomicExch(a.status, AZ_ETIMEOUT); break; }
+                fr_stage_planes<G>(a, tm, td, g, reinterpret_cast<uint32_t *>(pst + (size_t)s * fg.pstage_bytes),
+                                   hdrs + s * (kFrStageHeader / 4), fg, &pfull[s], &ctr[s]);
+            }
+        }
+        if (stop && lane == 0) {
+            *abort_flag = 1;
+            // grace for this CTA's own copies still in flight
+            for (uint32_t jj = j > (uint32_t)S ? j - S : 0; jj < j; ++jj) fr_drain(&pfull[jj % S], (jj / S) & 1);
+            for (int kk = issued > 2 ? issued - 2 : 0; kk < issued; ++kk) fr_drain(&efull[kk & 1], (uint32_t)((kk >> 1) & 1));
+        }
+    } else {
+        int k = 0;
+        uint32_t j = 0;
+        bool stop = false;
+        for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x, ++k) {
+            const int eb = k & 1;
+            bool ok = mbar_wait_bounded(&efull[eb], (uint32_t)((k >> 1) & 1));
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok || *abort_flag != 0) {
+                if (!ok && lane == 0) { atomicExch(a.status, AZ_ETIMEOUT); *abort_flag = 1; }
+                break;
+            }
+            const unsigned char *ebp = ebuf0 + (size_t)eb * fg.ebuf_bytes;
+            for (int g = 0; g < a.n_groups; ++g, ++j) {
+                const int s = (int)(j % (uint32_t)S);
+                ok = mbar_wait_bounded(&pfull[s], (j / S) & 1);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok || *abort_flag != 0) {
+                    if (!ok && lane == 0) { atomicExch(a.status, AZ_ETIMEOUT); *abort_flag = 1; }
+                    stop = true;
+                    break;
+                }
+                fr_consume<G, DT, DK>(a, fg, ebp, reinterpret_cast<const uint32_t *>(pst + (size_t)s * fg.pstage_bytes),
+                                      hdrs + s * (kFrStageHeader / 4), &ctr[s]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&pempty[s]);
+            }
+            if (stop) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&eempty[eb]);
         }
     }
 }
@@ -899,6 +1250,56 @@ int make_maps(const az_integrator *h, int engine, const void *img, int64_t rows_
 uint32_t plane_words_of(const az_integrator *h) { return plane_stride(h->tl.ss); }
 uint32_t rec_words_of(const az_integrator *h) { return (uint32_t)h->tl.max_rec_words; }
 
+// ---- frames kernel with tile-resident entries -----------------------------------------
+constexpr uint32_t kFrFixedBytes = 128 + 256;  // alignment slack; barriers, counters, flag
+
+// Sizes for G frames per plane stage; false unless two entry buffers and two plane stages fit.
+bool fr_geom(const az_integrator *h, int G, int dk, FrGeom &fg) {
+    fg.rec_cap = (rec_words_of(h) * 4u + 127u) & ~127u;
+    fg.ent_cap = ((uint32_t)h->tl.max_tile_entries + 7u) & ~7u;
+    fg.dk = dk;
+    fg.ebuf_bytes = (fg.rec_cap + fg.ent_cap * (dk ? 10u : 6u) + 127u) & ~127u;
+    fg.plane_words = plane_words_of(h);
+    fg.pstage_bytes = (uint32_t)G * fg.plane_words * 4u;
+    const int64_t avail = (int64_t)max_smem_per_block() - 2 * (int64_t)fg.ebuf_bytes - kFrFixedBytes;
+    const int64_t per = (int64_t)fg.pstage_bytes + kFrStageHeader;
+    fg.nstages = (int)std::min<int64_t>(kFrMaxStages, avail > 0 ? avail / per : 0);
+    return fg.nstages >= 2;
+}
+
+uint32_t fr_smem(const FrGeom &fg) {
+    return 2u * fg.ebuf_bytes + (uint32_t)fg.nstages * (fg.pstage_bytes + kFrStageHeader) + kFrFixedBytes;
+}
+
+template <int G, int DT, bool DK>
+int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s, Profiler *prof) {
+    if (a.n_tiles <= 0) return AZ_OK;
+    const uint32_t smem = fr_smem(fg);
+    auto kern = frames_kernel<G, DT, DK>;
+    AZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = std::min(a.n_tiles, num_sms());
+    {
+        ProfScope ps(prof, 0, s);
+        kern<<<grid, kFrThreads, smem, s>>>(a, fg, tm);
+    }
+    AZ_CUDA(cudaGetLastError());
+    return AZ_OK;
+}
+
+template <int G>
+int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s,
+                 Profiler *prof) {
+    const bool dk = a.ent_dark != nullptr;
+    switch (dtype) {
+        case AZ_DTYPE_F32:
+            return dk ? fr_launch<G, AZ_DTYPE_F32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_F32, false>(a, fg, tm, s, prof);
+        case AZ_DTYPE_U32:
+            return dk ? fr_launch<G, AZ_DTYPE_U32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_U32, false>(a, fg, tm, s, prof);
+        default:
+            return dk ? fr_launch<G, AZ_DTYPE_I32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_I32, false>(a, fg, tm, s, prof);
+    }
+}
+
 }  // namespace
 
 int num_sms() {
@@ -1020,6 +1421,46 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
                                 rec_words_of(h), stage_e, ent_dk);
     const int eng = engine_for(h);
+    if (eng == AZ_COPY_TMA) {
+        // tile-resident entries: G frames per plane stage, the largest of 16, 8, 4 not above
+        // the tuned frames per pass for which two stages fit
+        int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
+        FrGeom fg;
+        bool fits = fr_geom(h, G, ent_dk, fg);
+        while (!fits && G > 4) {
+            G >>= 1;
+            fits = fr_geom(h, G, ent_dk, fg);
+        }
+        if (fits) {
+            const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+            for (int f0 = 0; f0 < n; f0 += chunk) {
+                const int nf = std::min(chunk, n - f0);
+                Inst d = make_inst(h, false);
+                d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
+                d.n_frames = nf; d.fpi = G; d.n_groups = (nf + G - 1) / G;
+                d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
+                FrArgs a{};
+                a.img = d.img;
+                a.n_frames = nf; a.n_groups = d.n_groups; a.n_tiles = h->tl.n_active;
+                a.tile_desc = d.tile_desc; a.tile_rec = d.tile_rec;
+                a.ent_loc = d.ent_loc; a.ent_w = static_cast<const float *>(d.ent_w);
+                a.ent_dark = ent_dk ? h->tl.ent_dark.as<float>() : nullptr;
+                a.partial = static_cast<float *>(d.partial);
+                a.nseg = d.nseg; a.ny = d.ny; a.nx = d.nx; a.th = d.th; a.tw = d.tw; a.srow = d.srow;
+                a.ss = d.ss; a.ntx = d.ntx;
+                a.status = d.status;
+                TmaSet tm;
+                AZ_TRY(make_maps(h, eng, d.img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
+                switch (G) {
+                    case 4: AZ_TRY(fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof)); break;
+                    case 8: AZ_TRY(fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof)); break;
+                    default: AZ_TRY(fr_launch_dt<16>(dtype, a, fg, tm, s, &h->prof)); break;
+                }
+                AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
+            }
+            return AZ_OK;
+        }
+    }
     for (int f0 = 0; f0 < n; f0 += chunk_max) {
         const int nf = std::min(chunk_max, n - f0);
         Inst d = make_inst(h, false);
