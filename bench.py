@@ -142,7 +142,7 @@ def measured_peak():
 def ncu_traffic():
     """DRAM bytes per launch of the phase-1 frames kernel from the committed ncu summary,
     if that summary was taken on the current source of the kernel."""
-    path = os.path.join(ROOT, "profiles", "phase1_frames_pilatus6m.txt")
+    path = os.path.join(ROOT, "profiles", "frames_kernel_pilatus6m.txt")
     src = os.path.join(ROOT, "paper_1412_6367_gb300", "csrc", "integrate.cu")
     try:
         text = open(path).read()
@@ -336,7 +336,8 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (traffic_full * per_launch_frames / 64.0) if traffic_full else None,
-                "kernel": "phase1_kernel<float,float,MODE_FRAMES,%d,U32>" % info["frames_per_pass"],
+                "kernel": "frames_kernel<G=%d,U32,dark> (frames pass, %d frames per launch)" % (
+                    info["frames_per_pass"], int(per_launch_frames)),
                 "algorithmic_bytes_per_launch": ab, "peak_source": peak_kind + " hbm_gbs",
                 "kernel_share_of_step": tot_ms / ms if ms else None}
     step_bytes = algorithmic_bytes(info["nnz"], info["n_unmasked"], ig.nrows, B) + 3 * 4 * info["n_unmasked"]

@@ -310,7 +310,8 @@ int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_per_warp,
 /* Per-kernel totals recorded while profiling is enabled.  Kinds: 0 = phase-1 frames kernel
  * (az_integrate_batch*), 1 = phase-1 kernel of the frame-independent sums N and C,
  * 2 = phase-1 single-frame kernel (az_integrate1d/2d), 3 = phase-2 (finalise) kernel,
- * 4 = per-entry dark gather (once per az_integrate_batch* call given a dark). */
+ * 4 = per-call preparation (per-entry dark gather, per-pixel flat * solid angle *
+ * polarisation) of az_integrate_batch*. */
 #define AZ_PROF_KINDS 5
 typedef struct {
     int64_t launches[AZ_PROF_KINDS];

@@ -44,7 +44,7 @@ class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 5), ("total_ms", ctypes.c_double * 5)]
 
 
-PROFILE_KINDS = ("phase1_frames", "phase1_norm", "phase1_single", "phase2_finalize", "dark_gather")
+PROFILE_KINDS = ("phase1_frames", "phase1_norm", "phase1_single", "phase2_finalize", "prep")
 
 _lock = threading.Lock()
 _lib = None

@@ -96,6 +96,7 @@ struct TiledLayout {
     DevBuf ent_w64;         // double [padded_nnz]
     DevBuf ent_pix;         // int32  [padded_nnz] (pixel of the entry; -1 for padding)
     DevBuf ent_dark;        // float  [padded_nnz] (dark of the entry's pixel, per batch call)
+    DevBuf norm_frames;     // float  [2][ny][nx]: flat * solid angle * polarisation, then ones
     // Per active tile: a 32-byte descriptor {tile, record offset (words), record words,
     // entry offset, padded entry count, segment count, 0, 0} and a 16-byte aligned record
     // {tile, ns, entry offset, entry count, slot[ns], uint16 start[ns + 1]} that the forward

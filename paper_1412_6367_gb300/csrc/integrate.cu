@@ -1272,14 +1272,15 @@ uint32_t fr_smem(const FrGeom &fg) {
 }
 
 template <int G, int DT, bool DK>
-int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s, Profiler *prof) {
+int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s, Profiler *prof,
+              int prof_kind) {
     if (a.n_tiles <= 0) return AZ_OK;
     const uint32_t smem = fr_smem(fg);
     auto kern = frames_kernel<G, DT, DK>;
     AZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::min(a.n_tiles, num_sms());
     {
-        ProfScope ps(prof, 0, s);
+        ProfScope ps(prof, prof_kind, s);
         kern<<<grid, kFrThreads, smem, s>>>(a, fg, tm);
     }
     AZ_CUDA(cudaGetLastError());
@@ -1288,16 +1289,70 @@ int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t 
 
 template <int G>
 int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s,
-                 Profiler *prof) {
+                 Profiler *prof, int kind) {
     const bool dk = a.ent_dark != nullptr;
     switch (dtype) {
         case AZ_DTYPE_F32:
-            return dk ? fr_launch<G, AZ_DTYPE_F32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_F32, false>(a, fg, tm, s, prof);
+            return dk ? fr_launch<G, AZ_DTYPE_F32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_F32, false>(a, fg, tm, s, prof, kind);
         case AZ_DTYPE_U32:
-            return dk ? fr_launch<G, AZ_DTYPE_U32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_U32, false>(a, fg, tm, s, prof);
+            return dk ? fr_launch<G, AZ_DTYPE_U32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_U32, false>(a, fg, tm, s, prof, kind);
         default:
-            return dk ? fr_launch<G, AZ_DTYPE_I32, true>(a, fg, tm, s, prof) : fr_launch<G, AZ_DTYPE_I32, false>(a, fg, tm, s, prof);
+            return dk ? fr_launch<G, AZ_DTYPE_I32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_I32, false>(a, fg, tm, s, prof, kind);
     }
+}
+
+// Frames kernel over `nf` frames starting at `img` (nf <= the partial buffer's frames):
+// per-segment partials [nf][nseg] in h->partial.  Returns AZ_EUNSUPPORTED (without error
+// text) when the TMA engine or the shared memory it needs is not available.
+int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float *ent_dark,
+              int prof_kind, cudaStream_t s) {
+    if (engine_for(h) != AZ_COPY_TMA) return AZ_EUNSUPPORTED;
+    int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
+    FrGeom fg;
+    bool fits = fr_geom(h, G, ent_dark != nullptr, fg);
+    while (!fits && G > 4) {
+        G >>= 1;
+        fits = fr_geom(h, G, ent_dark != nullptr, fg);
+    }
+    if (!fits) return AZ_EUNSUPPORTED;
+    const TiledLayout &L = h->tl;
+    FrArgs a{};
+    a.img = static_cast<const char *>(img);
+    a.n_frames = nf; a.n_groups = (nf + G - 1) / G; a.n_tiles = L.n_active;
+    a.tile_desc = L.tile_desc.as<int32_t>(); a.tile_rec = L.tile_rec.as<int32_t>();
+    a.ent_loc = L.ent_loc.as<uint16_t>(); a.ent_w = L.ent_w32.as<float>();
+    a.ent_dark = ent_dark;
+    a.partial = h->partial.as<float>();
+    a.nseg = L.nseg; a.ny = h->ny; a.nx = h->nx; a.th = L.th; a.tw = L.tw; a.srow = L.srow;
+    a.ss = L.ss; a.ntx = L.ntx;
+    a.status = h->status.as<int>();
+    TmaSet tm;
+    AZ_TRY(make_maps(h, AZ_COPY_TMA, img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
+    switch (G) {
+        case 4: return fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof, prof_kind);
+        case 8: return fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof, prof_kind);
+        default: return fr_launch_dt<16>(dtype, a, fg, tm, s, &h->prof, prof_kind);
+    }
+}
+
+// flat * solid angle * polarisation per pixel, multiplied in that order from 1 (absent = 1):
+// the value the norm reduction multiplies by each weight.
+__global__ void norm_pixels_kernel(const float *__restrict__ flat, const float *__restrict__ sa,
+                                   const float *__restrict__ pol, int64_t n, float *__restrict__ out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float v = 1.f;
+        if (flat) v = __fmul_rn(v, flat[p]);
+        if (sa) v = __fmul_rn(v, sa[p]);
+        if (pol) v = __fmul_rn(v, pol[p]);
+        out[p] = v;
+    }
+}
+
+__global__ void fill_f32_kernel(float *__restrict__ out, int64_t n, float v) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        out[p] = v;
 }
 
 }  // namespace
@@ -1378,6 +1433,29 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
     Inst d = make_inst(h, false);
     d.flat = flat; d.sa = sa; d.pol = pol;
     d.oN = oN; d.oC = oC;
+    if (engine_for(h) == AZ_COPY_TMA && h->partial_bytes >= 2 * sizeof(float) * (size_t)h->tl.nseg) {
+        // N and C as a two-frame batch through the frames kernel: frame 0 holds
+        // flat * solid angle * polarisation per pixel, frame 1 ones.  Each weight meets the
+        // same value as in the norm mode below, through the same accumulation.
+        const int64_t npix = (int64_t)h->ny * h->nx;
+        const int64_t blocks = std::min<int64_t>((npix + 255) / 256, (int64_t)num_sms() * 8);
+        if (h->tl.norm_frames.bytes < 2 * sizeof(float) * (size_t)npix) {
+            AZ_TRY(h->tl.norm_frames.alloc(2 * sizeof(float) * (size_t)npix));
+            fill_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(h->tl.norm_frames.as<float>() + npix, npix, 1.f);
+            AZ_CUDA(cudaGetLastError());
+        }
+        {
+            ProfScope ps(&h->prof, 4, s);
+            norm_pixels_kernel<<<(unsigned)blocks, 256, 0, s>>>(flat, sa, pol, npix, h->tl.norm_frames.as<float>());
+            AZ_CUDA(cudaGetLastError());
+        }
+        const int rc = frames_v3(h, h->tl.norm_frames.p, 2, AZ_DTYPE_F32, nullptr, 1, s);
+        if (rc == AZ_OK) {
+            AZ_TRY((run_phase2<float, MODE_NORM>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
+            return AZ_OK;
+        }
+        if (rc != AZ_EUNSUPPORTED) return rc;
+    }
     const int planes = (flat != nullptr) + (sa != nullptr) + (pol != nullptr);
     StageGeom sg = choose_stage(plane_words_of(h), planes, (uint32_t)h->tl.max_tile_entries, 4,
                                 rec_words_of(h), d.stage_entries);
@@ -1422,43 +1500,19 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
                                 rec_words_of(h), stage_e, ent_dk);
     const int eng = engine_for(h);
     if (eng == AZ_COPY_TMA) {
-        // tile-resident entries: G frames per plane stage, the largest of 16, 8, 4 not above
-        // the tuned frames per pass for which two stages fit
-        int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
-        FrGeom fg;
-        bool fits = fr_geom(h, G, ent_dk, fg);
-        while (!fits && G > 4) {
-            G >>= 1;
-            fits = fr_geom(h, G, ent_dk, fg);
-        }
-        if (fits) {
-            const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
-            for (int f0 = 0; f0 < n; f0 += chunk) {
-                const int nf = std::min(chunk, n - f0);
-                Inst d = make_inst(h, false);
-                d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
-                d.n_frames = nf; d.fpi = G; d.n_groups = (nf + G - 1) / G;
-                d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
-                FrArgs a{};
-                a.img = d.img;
-                a.n_frames = nf; a.n_groups = d.n_groups; a.n_tiles = h->tl.n_active;
-                a.tile_desc = d.tile_desc; a.tile_rec = d.tile_rec;
-                a.ent_loc = d.ent_loc; a.ent_w = static_cast<const float *>(d.ent_w);
-                a.ent_dark = ent_dk ? h->tl.ent_dark.as<float>() : nullptr;
-                a.partial = static_cast<float *>(d.partial);
-                a.nseg = d.nseg; a.ny = d.ny; a.nx = d.nx; a.th = d.th; a.tw = d.tw; a.srow = d.srow;
-                a.ss = d.ss; a.ntx = d.ntx;
-                a.status = d.status;
-                TmaSet tm;
-                AZ_TRY(make_maps(h, eng, d.img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
-                switch (G) {
-                    case 4: AZ_TRY(fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof)); break;
-                    case 8: AZ_TRY(fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof)); break;
-                    default: AZ_TRY(fr_launch_dt<16>(dtype, a, fg, tm, s, &h->prof)); break;
-                }
-                AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
-            }
-            return AZ_OK;
+        // tile-resident entries (frames_kernel), up to 64 frames per launch
+        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+        for (int f0 = 0; f0 < n; f0 += chunk) {
+            const int nf = std::min(chunk, n - f0);
+            Inst d = make_inst(h, false);
+            d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
+            const int rc = frames_v3(h, d.img, nf, dtype, ent_dk ? h->tl.ent_dark.as<float>() : nullptr, 0, s);
+            if (rc == AZ_EUNSUPPORTED && f0 == 0) break;  // the general kernel below
+            AZ_TRY(rc);
+            d.n_frames = nf;
+            d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
+            AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
+            if (f0 + nf >= n) return AZ_OK;
         }
     }
     for (int f0 = 0; f0 < n; f0 += chunk_max) {
