@@ -36,7 +36,7 @@ METRIC = "Pilatus-6M-shape 1D integration frames/s & HBM GB/s vs plain, <=1e-5 r
 UNIT = "frames/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -55,6 +55,30 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def frame_seeds(rank, n=8):
+    """Seeds of the synthetic frames a rank cycles through (disjoint across ranks): each rank
+    integrates its own frames, there is no exchange between ranks."""
+    return [1000 * rank + k for k in range(n)]
+
+
+def max_over_ranks(value, world):
+    """The largest of every rank's `value` (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
+        else torch.device("cpu")
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(frames_per_rank_step, world, steps, ms):
+    """Frames per second of the whole job: every rank's frames over the slowest rank's time."""
+    return world * frames_per_rank_step * steps / (ms / 1e3)
 
 
 def workload_inputs(w, og_positions):
@@ -268,7 +292,7 @@ def main():
     sa_d = g.solid_angle(w.ny, w.nx, device=dev)
     pol_d = g.polarization(w.ny, w.nx, w.polarization_factor, device=dev)
     B = args.frames
-    base = np.stack([synth.ring_image(crad, seed=1000 * rank + k) for k in range(8)])
+    base = np.stack([synth.ring_image(crad, seed=sd) for sd in frame_seeds(rank)])
     frames_i32 = torch.empty((B, w.ny, w.nx), dtype=torch.int32, device=dev)
     fb = torch.from_numpy(base.view(np.int32)).to(dev)
     for k in range(B):
@@ -315,20 +339,14 @@ def main():
     ig.profile_enable(False)
     clk = clocks.stop()
     prof = ig.profile_read()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
     ms_per_step = ms / args.steps
-    value = world * B * args.steps / (ms / 1e3)
+    value = whole_job_rate(B, world, args.steps, ms)
 
     # roofline of the dominant kernel (phase-1 frames): algorithmic bytes / mean duration
     peak, peak_kind = measured_peak()
     n_launch, tot_ms = prof["phase1_frames"]
     launches_per_step = sum(v[0] for v in prof.values()) / args.steps
-    chunk = min(B, 64)
     per_launch_frames = B * args.steps / max(n_launch, 1)
     ab = phase1_frames_bytes(info["nnz"], info["n_unmasked"], per_launch_frames)
     achieved = ab / (tot_ms / max(n_launch, 1) / 1e3) / 1e9 if n_launch else None
