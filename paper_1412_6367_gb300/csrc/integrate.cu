@@ -524,12 +524,81 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
     }
 }
 
+// FP64 single-frame reduction with one lane per segment forming all three sums.  The FP64
+// pipe of this GPU is narrow, and the one-lane-per-quantity form of consume_serial leaves
+// three of four lanes idle in every FP64 instruction; here every lane works.  Per sum the
+// operations are those of consume_serial in single mode: x = image - dark,
+// n = ((1 flat) solid angle) polarisation, 1, each multiplied by the weight into accumulator
+// e mod 4, merged as ((a0 + a1) + (a2 + a3)).
+template <int DT, bool SE>
+__device__ void consume_single64(const ConsumerParams &cp, const unsigned char *stage,
+                                 const StageGeom &sg, int *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int *h = reinterpret_cast<const int *>(stage);
+    const int ns = h[0];
+    const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
+    const int oimg = h[16];
+    const int *slots = reinterpret_cast<const int *>(stage + kHeaderBytes) + 4;
+    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
+    const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
+    const uint16_t *L;
+    const double *W;
+    if constexpr (SE) {
+        const unsigned char *eb = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
+        L = reinterpret_cast<const uint16_t *>(eb);
+        W = reinterpret_cast<const double *>(eb + sg.ent_cap * 2u);
+    } else {
+        L = cp.ent_loc + h[8];
+        W = static_cast<const double *>(cp.ent_w) + h[8];
+    }
+    double *out = static_cast<double *>(cp.partial);
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, 32);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        const int sl = b + lane;
+        const bool live = sl < ns;
+        const int e0 = live ? starts[sl] : 0, e1 = live ? starts[sl + 1] : 0, slot = live ? slots[sl] : 0;
+        double aS[4] = {0.0, 0.0, 0.0, 0.0}, aN[4] = {0.0, 0.0, 0.0, 0.0}, aC[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int qd = e0; qd < e1; qd += 4) {
+            const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
+            const int loc[4] = {(int)(l2.x & 0xffffu), (int)(l2.x >> 16), (int)(l2.y & 0xffffu),
+                                (int)(l2.y >> 16)};
+            double w[4];
+            W4<double>::load(W + qd, w);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                double x = img_f64<DT>(planes[oimg + loc[j]]);
+                if (odark >= 0) x = x - (double)__uint_as_float(planes[odark + loc[j]]);
+                double n = 1.0;
+                if (oflat >= 0) n = n * (double)__uint_as_float(planes[oflat + loc[j]]);
+                if (osa >= 0) n = n * (double)__uint_as_float(planes[osa + loc[j]]);
+                if (opol >= 0) n = n * (double)__uint_as_float(planes[opol + loc[j]]);
+                aS[j] = __fma_rn(w[j], x, aS[j]);
+                aN[j] = __fma_rn(w[j], n, aN[j]);
+                aC[j] = __fma_rn(w[j], 1.0, aC[j]);
+            }
+        }
+        if (live) {
+            out[slot] = (aS[0] + aS[1]) + (aS[2] + aS[3]);
+            out[(size_t)cp.nseg + slot] = (aN[0] + aN[1]) + (aN[2] + aN[3]);
+            out[2 * (size_t)cp.nseg + slot] = (aC[0] + aC[1]) + (aC[2] + aC[3]);
+        }
+    }
+}
+
 template <class AT, class WT, int MODE, int NIMG, int DT>
 __device__ __forceinline__ void consume_dispatch(const ConsumerParams &cp, const unsigned char *stage,
                                                  const StageGeom &sg, int *ctr) {
-    constexpr int Q = MODE == MODE_FRAMES ? NIMG : (MODE == MODE_NORM ? 2 : 4);
-    if (cp.stage_entries) consume_serial<Q, AT, WT, MODE, DT, true>(cp, stage, sg, ctr);
-    else consume_serial<Q, AT, WT, MODE, DT, false>(cp, stage, sg, ctr);
+    if constexpr (MODE == MODE_SINGLE && sizeof(AT) == 8) {
+        if (cp.stage_entries) consume_single64<DT, true>(cp, stage, sg, ctr);
+        else consume_single64<DT, false>(cp, stage, sg, ctr);
+    } else {
+        constexpr int Q = MODE == MODE_FRAMES ? NIMG : (MODE == MODE_NORM ? 2 : 4);
+        if (cp.stage_entries) consume_serial<Q, AT, WT, MODE, DT, true>(cp, stage, sg, ctr);
+        else consume_serial<Q, AT, WT, MODE, DT, false>(cp, stage, sg, ctr);
+    }
 }
 
 // Warp-specialised persistent kernel.  Warp 0 produces: for each work item of this CTA
