@@ -239,12 +239,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase; returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
-                                                  uint32_t max_iter = (1u << 24)) {
-    for (uint32_t it = 0; it < max_iter; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
+// One try with the thread suspended by the hardware until the phase completes or `hint_ns`
+// nanoseconds pass (no polling loop keeps the warp issuing while it waits).
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: gives up (returns false) after about two seconds of
+// the SM's clock, however long each suspended try lasts.
+constexpr long long kWaitLimitCycles = 4000000000LL;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait_hint(bar, parity, 1000000u)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait_hint(bar, parity, 1000000u))
+        if (clock64() - t0 > kWaitLimitCycles) return false;
+    return true;
 }
 
 // Bulk (non-tensor) TMA copy global -> shared; 16-byte aligned addresses, size % 16 == 0.
