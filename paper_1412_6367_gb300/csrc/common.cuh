@@ -146,6 +146,7 @@ struct az_integrator {
     azint::TiledLayout tl;
     // tuning
     int rows_per_warp = 4, frames_per_pass = 8, copy_engine = AZ_COPY_TMA;
+    bool count_ready = false;  // norm[nrows..] holds C for the current tiled layout
     // scratch: per-segment partial sums and per-row frame-independent sums
     azint::DevBuf partial;     // float or double [planes][nseg]
     size_t partial_bytes = 0;

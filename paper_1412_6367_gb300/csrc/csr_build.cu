@@ -992,6 +992,7 @@ int build_integrator(int ny, int nx, const double *rad, const double *chi, int n
 
 int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     TiledLayout &L = h->tl;
+    h->count_ready = false;  // the accumulation order of C depends on the layout
     const int64_t nnz = h->nnz;
     if (th < 4 || (th % 4) != 0 || tw < 4 || (tw % 4) != 0)
         return fail(AZ_EINVAL, "tile %dx%d: both sides must be positive multiples of 4", th, tw);

@@ -56,6 +56,7 @@ struct Inst {
     float *norm;         // [2][nrows] N, C (FP32 batched path)
     void *oI, *oS, *oN, *oC;
     int frame_out0;      // first output frame of this launch
+    int norm_rows;       // norm pass: 2 = partials hold N and C, 1 = N only
     int64_t item_begin, row_begin;
     int n_items;
     int stage_entries;
@@ -702,6 +703,7 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
 constexpr int kFrConsumers = 16;
 constexpr int kFrThreads = 32 * (1 + kFrConsumers);
 constexpr int kFrMaxStages = 8;
+constexpr int kFrMaxEbufs = 6;
 constexpr uint32_t kFrStageHeader = 128;  // per plane stage: nimg, group, G plane offsets
 
 struct FrArgs {
@@ -719,6 +721,7 @@ struct FrGeom {
     uint32_t rec_cap;       // bytes for the tile record (multiple of 128)
     uint32_t ent_cap;       // entry capacity (multiple of 8)
     uint32_t ebuf_bytes;    // one entry buffer (multiple of 128)
+    int nebufs;             // entry buffers in the ring (2 .. kFrMaxEbufs)
     uint32_t plane_words;   // words per plane
     uint32_t pstage_bytes;  // one plane stage: G planes
     int nstages;            // plane stages
@@ -935,18 +938,19 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
         (reinterpret_cast<uintptr_t>(smem_raw) + 127u) & ~static_cast<uintptr_t>(127u));
     const int S = fg.nstages;
     unsigned char *ebuf0 = smem;
-    unsigned char *pst = smem + 2 * (size_t)fg.ebuf_bytes;
+    const int NE = fg.nebufs;
+    unsigned char *pst = smem + (size_t)NE * fg.ebuf_bytes;
     int *hdrs = reinterpret_cast<int *>(pst + (size_t)S * fg.pstage_bytes);
     uint64_t *efull = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(hdrs) +
                                                    (size_t)S * kFrStageHeader);
-    uint64_t *eempty = efull + 2;
-    uint64_t *pfull = eempty + 2;
+    uint64_t *eempty = efull + NE;
+    uint64_t *pfull = eempty + NE;
     uint64_t *pempty = pfull + S;
     int *ctr = reinterpret_cast<int *>(pempty + S);
     volatile int *abort_flag = ctr + S;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NE; ++i) {
             mbar_init(&efull[i], 1);
             mbar_init(&eempty[i], kFrConsumers);
         }
@@ -965,9 +969,9 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
         bool stop = false;
         for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x, ++k) {
             const TileDesc td = fr_desc(a, item);
-            const int eb = k & 1;
+            const int eb = k % NE;
             bool ok = true;
-            if (k >= 2) ok = mbar_wait_bounded(&eempty[eb], (uint32_t)(((k >> 1) - 1) & 1));
+            if (k >= NE) ok = mbar_wait_bounded(&eempty[eb], (uint32_t)(((k / NE) - 1) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok || *abort_flag != 0) { stop = true; if (!ok && lane == 0) atomicExch(a.status, AZ_ETIMEOUT); break; }
             if (lane == 0) fr_stage_entries(a, fg, td, ebuf0 + (size_t)eb * fg.ebuf_bytes, &efull[eb]);
@@ -986,15 +990,16 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
             *abort_flag = 1;
             // grace for this CTA's own copies still in flight
             for (uint32_t jj = j > (uint32_t)S ? j - S : 0; jj < j; ++jj) fr_drain(&pfull[jj % S], (jj / S) & 1);
-            for (int kk = issued > 2 ? issued - 2 : 0; kk < issued; ++kk) fr_drain(&efull[kk & 1], (uint32_t)((kk >> 1) & 1));
+            for (int kk = issued > NE ? issued - NE : 0; kk < issued; ++kk)
+                fr_drain(&efull[kk % NE], (uint32_t)((kk / NE) & 1));
         }
     } else {
         int k = 0;
         uint32_t j = 0;
         bool stop = false;
         for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x, ++k) {
-            const int eb = k & 1;
-            bool ok = mbar_wait_bounded(&efull[eb], (uint32_t)((k >> 1) & 1));
+            const int eb = k % NE;
+            bool ok = mbar_wait_bounded(&efull[eb], (uint32_t)((k / NE) & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (!ok || *abort_flag != 0) {
                 if (!ok && lane == 0) { atomicExch(a.status, AZ_ETIMEOUT); *abort_flag = 1; }
@@ -1084,12 +1089,14 @@ __global__ void phase2_kernel(const __grid_constant__ Inst single, const Inst *_
                 }
             } else {
                 const AT N = row_sum<AT>(P, a, b);
-                const AT C = row_sum<AT>(P + d.nseg, a, b);
+                const AT C = d.norm_rows == 2 ? row_sum<AT>(P + d.nseg, a, b) : AT(0);
                 if (lane == 0) {
                     d.norm[r] = (float)N;
-                    d.norm[d.nrows + r] = (float)C;
                     if (d.oN) static_cast<float *>(d.oN)[r] = (float)N;
-                    if (d.oC) static_cast<float *>(d.oC)[r] = (float)C;
+                    if (d.norm_rows == 2) {
+                        d.norm[d.nrows + r] = (float)C;
+                        if (d.oC) static_cast<float *>(d.oC)[r] = (float)C;
+                    }
                 }
             }
         }
@@ -1154,6 +1161,7 @@ Inst make_inst(const az_integrator *h, bool fp64) {
     d.rpw = 32 / h->frames_per_pass; d.nseg = L.nseg; d.nrows = h->nrows;
     d.npix = (int64_t)h->ny * h->nx;
     d.n_frames = 1; d.fpi = 1; d.n_groups = 1;
+    d.norm_rows = 2;
     d.partial = h->partial.p;
     d.norm = h->norm.as<float>();
     d.status = h->status.as<int>();
@@ -1320,24 +1328,33 @@ uint32_t plane_words_of(const az_integrator *h) { return plane_stride(h->tl.ss);
 uint32_t rec_words_of(const az_integrator *h) { return (uint32_t)h->tl.max_rec_words; }
 
 // ---- frames kernel with tile-resident entries -----------------------------------------
-constexpr uint32_t kFrFixedBytes = 128 + 256;  // alignment slack; barriers, counters, flag
+constexpr uint32_t kFrFixedBytes = 128 + 384;  // alignment slack; barriers, counters, flag
 
 // Sizes for G frames per plane stage; false unless two entry buffers and two plane stages fit.
-bool fr_geom(const az_integrator *h, int G, int dk, FrGeom &fg) {
+bool fr_geom(const az_integrator *h, int G, int dk, int n_groups, FrGeom &fg) {
     fg.rec_cap = (rec_words_of(h) * 4u + 127u) & ~127u;
     fg.ent_cap = ((uint32_t)h->tl.max_tile_entries + 7u) & ~7u;
     fg.dk = dk;
     fg.ebuf_bytes = (fg.rec_cap + fg.ent_cap * (dk ? 10u : 6u) + 127u) & ~127u;
     fg.plane_words = plane_words_of(h);
     fg.pstage_bytes = (uint32_t)G * fg.plane_words * 4u;
-    const int64_t avail = (int64_t)max_smem_per_block() - 2 * (int64_t)fg.ebuf_bytes - kFrFixedBytes;
+    // two entry buffers and as many plane stages as fit; then, when a work item has few
+    // frame groups (the entries dominate its copies), more entry buffers in what is left
     const int64_t per = (int64_t)fg.pstage_bytes + kFrStageHeader;
+    const int64_t avail = (int64_t)max_smem_per_block() - 2 * (int64_t)fg.ebuf_bytes - kFrFixedBytes;
     fg.nstages = (int)std::min<int64_t>(kFrMaxStages, avail > 0 ? avail / per : 0);
+    fg.nebufs = 2;
+    if (n_groups <= 2 && fg.nstages >= 2) {
+        fg.nstages = 2;
+        const int64_t left = avail - 2 * per;
+        fg.nebufs = 2 + (int)std::min<int64_t>(kFrMaxEbufs - 2, left / (int64_t)fg.ebuf_bytes);
+    }
     return fg.nstages >= 2;
 }
 
 uint32_t fr_smem(const FrGeom &fg) {
-    return 2u * fg.ebuf_bytes + (uint32_t)fg.nstages * (fg.pstage_bytes + kFrStageHeader) + kFrFixedBytes;
+    return (uint32_t)fg.nebufs * fg.ebuf_bytes + (uint32_t)fg.nstages * (fg.pstage_bytes + kFrStageHeader) +
+           kFrFixedBytes;
 }
 
 template <int G, int DT, bool DK>
@@ -1378,10 +1395,15 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     if (engine_for(h) != AZ_COPY_TMA) return AZ_EUNSUPPORTED;
     int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
     FrGeom fg;
-    bool fits = fr_geom(h, G, ent_dark != nullptr, fg);
-    while (!fits && G > 4) {
+    // one or two frames of float values without a dark (the norm pass): one lane per
+    // segment and frame, 32 / nf segments per warp
+    const bool small = nf <= 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr;
+    if (small) G = nf;
+    else if (nf < G) G = nf <= 4 ? 4 : (nf <= 8 ? 8 : G);
+    bool fits = fr_geom(h, G, ent_dark != nullptr, (nf + G - 1) / G, fg);
+    while (!fits && G > 4 && !small) {
         G >>= 1;
-        fits = fr_geom(h, G, ent_dark != nullptr, fg);
+        fits = fr_geom(h, G, ent_dark != nullptr, (nf + G - 1) / G, fg);
     }
     if (!fits) return AZ_EUNSUPPORTED;
     const TiledLayout &L = h->tl;
@@ -1397,6 +1419,9 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     a.status = h->status.as<int>();
     TmaSet tm;
     AZ_TRY(make_maps(h, AZ_COPY_TMA, img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
+    if (small)
+        return G == 1 ? fr_launch<1, AZ_DTYPE_F32, false>(a, fg, tm, s, &h->prof, prof_kind)
+                      : fr_launch<2, AZ_DTYPE_F32, false>(a, fg, tm, s, &h->prof, prof_kind);
     switch (G) {
         case 4: return fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof, prof_kind);
         case 8: return fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof, prof_kind);
@@ -1503,10 +1528,21 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
     d.flat = flat; d.sa = sa; d.pol = pol;
     d.oN = oN; d.oC = oC;
     if (engine_for(h) == AZ_COPY_TMA && h->partial_bytes >= 2 * sizeof(float) * (size_t)h->tl.nseg) {
-        // N and C as a two-frame batch through the frames kernel: frame 0 holds
-        // flat * solid angle * polarisation per pixel, frame 1 ones.  Each weight meets the
-        // same value as in the norm mode below, through the same accumulation.
+        // Through the frames kernel.  C = sum w does not depend on the inputs: the first call
+        // after a layout change reduces [flat * solid angle * polarisation; ones] as a
+        // two-frame batch and keeps C; later calls reduce the first frame only (N), and
+        // without flat, solid angle and polarisation N equals C.  Each weight meets the same
+        // value as in the norm mode below, through the same accumulation.
         const int64_t npix = (int64_t)h->ny * h->nx;
+        const int nrows = h->nrows;
+        float *Cdev = h->norm.as<float>() + nrows;
+        const bool corr = flat || sa || pol;
+        if (h->count_ready && !corr) {
+            AZ_CUDA(cudaMemcpyAsync(h->norm.as<float>(), Cdev, sizeof(float) * nrows, cudaMemcpyDeviceToDevice, s));
+            if (oN) AZ_CUDA(cudaMemcpyAsync(oN, Cdev, sizeof(float) * nrows, cudaMemcpyDeviceToDevice, s));
+            if (oC) AZ_CUDA(cudaMemcpyAsync(oC, Cdev, sizeof(float) * nrows, cudaMemcpyDeviceToDevice, s));
+            return AZ_OK;
+        }
         const int64_t blocks = std::min<int64_t>((npix + 255) / 256, (int64_t)num_sms() * 8);
         if (h->tl.norm_frames.bytes < 2 * sizeof(float) * (size_t)npix) {
             AZ_TRY(h->tl.norm_frames.alloc(2 * sizeof(float) * (size_t)npix));
@@ -1518,9 +1554,13 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
             norm_pixels_kernel<<<(unsigned)blocks, 256, 0, s>>>(flat, sa, pol, npix, h->tl.norm_frames.as<float>());
             AZ_CUDA(cudaGetLastError());
         }
-        const int rc = frames_v3(h, h->tl.norm_frames.p, 2, AZ_DTYPE_F32, nullptr, 1, s);
+        const int nf = h->count_ready ? 1 : 2;
+        const int rc = frames_v3(h, h->tl.norm_frames.p, nf, AZ_DTYPE_F32, nullptr, 1, s);
         if (rc == AZ_OK) {
+            d.norm_rows = nf;
             AZ_TRY((run_phase2<float, MODE_NORM>(d, nullptr, 1, h->nrows, 1, s, &h->prof)));
+            if (nf == 1 && oC) AZ_CUDA(cudaMemcpyAsync(oC, Cdev, sizeof(float) * nrows, cudaMemcpyDeviceToDevice, s));
+            h->count_ready = true;
             return AZ_OK;
         }
         if (rc != AZ_EUNSUPPORTED) return rc;
