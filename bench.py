@@ -47,6 +47,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the cake / batching / stream / adjoint measurements")
     return ap.parse_args(argv)
 
 
@@ -251,6 +253,81 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _event_ms(torch, fn, reps):
+    """Mean device time of fn() over `reps` calls (CUDA events on the current stream)."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
+    """The other workloads' throughput (device-resident inputs, warm), reported beside the
+    headline: the 2D cake, the 64-instance persistent launch, a 4096-frame stream through
+    one matrix, and the adjoint on the Pilatus matrix."""
+    from paper_1412_6367_gb300 import api, synth
+    out = {}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+
+    # cake: 2048 x 2048 float32, 500 x 360 bins, full split, corrections
+    w = synth.cake_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, w.npt_azim, "2th_deg", "full", device=dev)
+    dark = torch.rand((w.ny, w.nx), generator=gen, device=dev) + 10.0
+    flat = 0.95 + 0.1 * torch.rand((w.ny, w.nx), generator=gen, device=dev)
+    sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
+    frames = 1000.0 * torch.rand((64, w.ny, w.nx), generator=gen, device=dev)
+    for _ in range(3):
+        ig.integrate_batch(frames, dark, flat, sa, pol)
+    ms = _event_ms(torch, lambda: ig.integrate_batch(frames, dark, flat, sa, pol), 5)
+    ms1 = _event_ms(torch, lambda: ig.integrate(frames[0], dark, flat, sa, pol, precision="fp32"), 10)
+    out["cake_2048x2048_500x360"] = {"batched_frames_per_s": 64 / (ms / 1e3),
+                                      "single_frame_fp32_ms": ms1, "nnz": ig.info["nnz"]}
+    del frames, ig
+
+    # 64 heterogeneous instances in one graph-captured persistent launch
+    ws = synth.batch_instances()
+    igs, imgs = [], []
+    for wi in ws:
+        gi = api.Geometry(*wi.geometry.astuple())
+        igs.append(api.Integrator.build(gi, (wi.ny, wi.nx), wi.npt_rad, 0, "q_nm^-1", "full", device=dev))
+        imgs.append(torch.randint(0, 4000, (wi.ny, wi.nx), generator=gen, device=dev, dtype=torch.int32))
+    plan = api.MultiPlan(igs, imgs)
+    for _ in range(3):
+        plan.launch(use_graph=True)
+    ms = _event_ms(torch, lambda: plan.launch(use_graph=True), 10)
+    pix = sum(wi.ny * wi.nx for wi in ws)
+    out["batching_64_instances"] = {"ms_per_launch": ms, "instances_per_s": 64 / (ms / 1e3),
+                                    "gpix_per_s": pix / (ms / 1e3) / 1e9}
+    del plan, igs, imgs
+
+    # 4096 frames of 2167 x 2070 uint32 through one matrix (2000 q bins): a 256-frame device
+    # buffer integrated 16 times
+    w = synth.stream_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "full", device=dev)
+    buf = torch.randint(0, 4000, (256, w.ny, w.nx), generator=gen, device=dev, dtype=torch.int32)
+    fr = buf.view(torch.uint32)
+    ig.integrate_batch(fr[:64])
+    ms = _event_ms(torch, lambda: ig.integrate_batch(fr), 16)
+    out["stream_4096x2167x2070"] = {"frames_per_s": 256 / (ms / 1e3), "ms_per_4096": 16 * ms}
+    del buf, fr, ig
+
+    # adjoint (image and flat-field gradients) on the Pilatus matrix, FP32 and FP64
+    img, dark, flat, sa, pol = pilatus_inputs
+    for prec in ("fp32", "fp64"):
+        res = ig_pilatus.integrate(img, dark, flat, sa, pol, precision=prec)
+        gI = torch.ones_like(res.I)
+        ig_pilatus.backward(gI, res.I, res.sum_norm, sa, pol, prec)
+        ms = _event_ms(torch, lambda: ig_pilatus.backward(gI, res.I, res.sum_norm, sa, pol, prec), 10)
+        out["backward_pilatus_" + prec] = {"ms_per_call": ms}
+    return out
+
+
 def config_dict(w, frames):
     return {"workload": "%s: %dx%d uint32, module-gap mask, q nm^-1, %d bins, full split, "
                         "dark/flat/solid-angle/polarisation" % (w.name, w.ny, w.nx, w.npt_rad),
@@ -299,6 +376,7 @@ def main():
         frames_i32[k].copy_(fb[k % 8])
     del fb
     frames = frames_i32.view(torch.uint32)  # the counts are uint32; moved as int32 bits
+    fb0 = frames_i32[0].clone().view(torch.uint32)
     out = api.Result(torch.empty((B, ig.nrows), device=dev), torch.empty((B, ig.nrows), device=dev),
                      torch.empty(ig.nrows, device=dev), torch.empty(ig.nrows, device=dev))
 
@@ -397,6 +475,12 @@ def main():
                "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(2 * oI.numel() * 4),
                "frames_per_step": Be, "api": "az_integrate_batch_host"}
 
+    others = None
+    if rank == 0 and not args.no_other_workloads:
+        del frames_i32, frames, out
+        torch.cuda.empty_cache()
+        others = other_workloads(torch, dev, ig, (fb0, dark_d, flat_d, sa_d, pol_d))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = cpu_baseline(w, args.cpu_seconds)
@@ -414,7 +498,8 @@ def main():
                           "segments": info["n_segments"], "tile": [info["tile_h"], info["tile_w"]],
                           "rows_per_warp": info["rows_per_warp"],
                           "frames_per_pass": info["frames_per_pass"], "autotune_ms_per_frame": tuned},
-                "kernel_ms": {k: v for k, v in prof.items()}}
+                "kernel_ms": {k: v for k, v in prof.items()},
+                "other_workloads": others}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

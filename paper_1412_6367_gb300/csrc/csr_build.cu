@@ -781,18 +781,6 @@ __global__ void scatter_slots_kernel(const int32_t *__restrict__ perm, int nseg,
         slot[perm[s]] = (int32_t)s;
 }
 
-__global__ void active_flags_kernel(const int32_t *cnt, int n, int32_t *flag) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x)
-        flag[t] = cnt[t] > 0;
-}
-
-__global__ void compact_kernel(const int32_t *flag, const int32_t *pos, int n, int32_t *out) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-         t += (int64_t)gridDim.x * blockDim.x)
-        if (flag[t]) out[pos[t]] = (int32_t)t;
-}
-
 __global__ void max_kernel(const int32_t *a, int n, int32_t *out) {
     __shared__ int32_t sm[32];
     int32_t m = 0;
@@ -812,29 +800,57 @@ __global__ void diff_kernel(const int32_t *ptr, int n, int32_t *out) {
         out[t] = ptr[t + 1] - ptr[t];
 }
 
-// Record size (int32 words, multiple of 4) of one active tile.
-__global__ void rec_words_kernel(const int32_t *__restrict__ active, int n_active,
-                                 const int32_t *__restrict__ tile_seg_ptr, int32_t *__restrict__ words) {
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_active;
+// Work items: a tile's segments (longest first) cut into runs whose entries, counted from
+// the run's first entry rounded down to a multiple of 8, stay within `cap` (a single longer
+// segment makes an item of its own).  One thread per tile; `fill` = 0 counts the items,
+// 1 writes (tile, first segment, end segment) for each.
+__global__ void chunk_kernel(const int32_t *__restrict__ tile_seg_ptr, const int32_t *__restrict__ seg_start,
+                             const int32_t *__restrict__ seg_end, int ntiles, int cap, int fill,
+                             int32_t *__restrict__ count, const int32_t *__restrict__ offs,
+                             int32_t *__restrict__ chunks) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int s0 = tile_seg_ptr[t], s1 = tile_seg_ptr[t + 1];
+        int n = 0, i = s0;
+        while (i < s1) {
+            const int e0 = seg_start[i] & ~7;
+            int j = i + 1;
+            while (j < s1 && seg_end[j] - e0 <= cap) ++j;
+            if (fill) {
+                int32_t *c = chunks + 3 * (size_t)(offs[t] + n);
+                c[0] = (int32_t)t; c[1] = i; c[2] = j;
+            }
+            ++n;
+            i = j;
+        }
+        if (!fill) count[t] = n;
+    }
+}
+
+// Record size (int32 words, multiple of 4) of one work item.
+__global__ void rec_words_kernel(const int32_t *__restrict__ chunks, int n_items, int32_t *__restrict__ words) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_items;
          a += (int64_t)gridDim.x * blockDim.x) {
-        const int t = active[a];
-        const int ns = tile_seg_ptr[t + 1] - tile_seg_ptr[t];
+        const int ns = chunks[3 * a + 2] - chunks[3 * a + 1];
         const int w = 4 + ns + (ns + 2) / 2;  // header, slots, uint16 starts[ns + 1]
         words[a] = (w + 3) & ~3;
     }
 }
 
-__global__ void rec_fill_kernel(const int32_t *__restrict__ active, int n_active,
-                                const int32_t *__restrict__ tile_seg_ptr,
-                                const int32_t *__restrict__ tile_ent_ptr,
+// Record {tile, ns, first entry, entries, slots[ns], uint16 starts[ns + 1]} and descriptor
+// {tile, record offset, record words, first entry, entries, ns} of one work item.  The
+// item's entries start at its first segment rounded down to a multiple of 8 entries (16-byte
+// aligned locations for the bulk copy) and end at its last segment's end rounded up to 8.
+__global__ void rec_fill_kernel(const int32_t *__restrict__ chunks, int n_items,
                                 const int32_t *__restrict__ seg_start, const int32_t *__restrict__ seg_end,
                                 const int32_t *__restrict__ seg_slot, const int32_t *__restrict__ rec_off,
-                                int32_t *__restrict__ rec, int32_t *__restrict__ desc) {
-    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_active;
+                                int32_t *__restrict__ rec, int32_t *__restrict__ desc,
+                                int32_t *__restrict__ item_entries, int32_t *__restrict__ item_segments) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n_items;
          a += (int64_t)gridDim.x * blockDim.x) {
-        const int t = active[a];
-        const int s0 = tile_seg_ptr[t], ns = tile_seg_ptr[t + 1] - s0;
-        const int e0 = tile_ent_ptr[t], ne = tile_ent_ptr[t + 1] - e0;
+        const int t = chunks[3 * a], s0 = chunks[3 * a + 1], ns = chunks[3 * a + 2] - s0;
+        const int e0 = seg_start[s0] & ~7;
+        const int ne = ((seg_end[s0 + ns - 1] - e0) + 7) & ~7;
         const int off = rec_off[a], words = rec_off[a + 1] - off;
         int32_t *r = rec + off;
         r[0] = t; r[1] = ns; r[2] = e0; r[3] = ne;
@@ -846,6 +862,8 @@ __global__ void rec_fill_kernel(const int32_t *__restrict__ active, int n_active
         int32_t *dd = desc + 8 * a;
         dd[0] = t; dd[1] = off; dd[2] = words; dd[3] = e0;
         dd[4] = ne; dd[5] = ns; dd[6] = 0; dd[7] = 0;
+        item_entries[a] = ne;
+        item_segments[a] = ns;
     }
 }
 
@@ -1136,55 +1154,66 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     AZ_TRY(L.row_slot_ptr.alloc(sizeof(int32_t) * (h->nrows + 1)));
     AZ_TRY(exclusive_scan_i32(rcnt.as<int32_t>(), L.row_slot_ptr.as<int32_t>(), h->nrows, s));
 
-    // active tiles and maxima
-    DevBuf aflag, apos, mx;
-    AZ_TRY(aflag.alloc(sizeof(int32_t) * ntiles));
-    AZ_TRY(apos.alloc(sizeof(int32_t) * (ntiles + 1)));
-    AZ_TRY(mx.alloc(sizeof(int32_t) * 2));
-    AZ_TRY(launch_gs(active_flags_kernel, ntiles, s, scnt.as<int32_t>(), ntiles, aflag.as<int32_t>()));
-    AZ_TRY(exclusive_scan_i32(aflag.as<int32_t>(), apos.as<int32_t>(), ntiles, s));
-    int32_t n_active = 0;
-    AZ_CUDA(cudaMemcpyAsync(&n_active, apos.as<int32_t>() + ntiles, sizeof(int32_t),
-                            cudaMemcpyDeviceToHost, s));
+    // Work items: a tile whose entries would not fit, twice, beside two stages of four frame
+    // planes in shared memory is cut at segment boundaries (about 11.5 bytes of shared memory
+    // per entry: location, weight, dark and its share of the record).
+    const int64_t plane_bytes = 4 * ((int64_t)4 * T.ss + 32);
+    const int64_t budget = ((int64_t)max_smem_per_block() - 1024 - 2 * (4 * plane_bytes + 256)) / 2;
+    const int kItemEntries = (int)std::max<int64_t>(1024, std::min<int64_t>(60000, budget * 2 / 23) & ~7);
+    DevBuf icnt, ioff, chunks, mx;
+    AZ_TRY(icnt.alloc(sizeof(int32_t) * ntiles));
+    AZ_TRY(ioff.alloc(sizeof(int32_t) * (ntiles + 1)));
+    AZ_TRY(mx.alloc(sizeof(int32_t) * 3));
+    AZ_TRY(launch_gs(chunk_kernel, ntiles, s, L.tile_seg_ptr.as<int32_t>(), L.seg_ent_ptr.as<int32_t>(),
+                     L.seg_ent_ptr.as<int32_t>() + nseg, ntiles, kItemEntries, 0, icnt.as<int32_t>(),
+                     (const int32_t *)nullptr, (int32_t *)nullptr));
+    AZ_TRY(exclusive_scan_i32(icnt.as<int32_t>(), ioff.as<int32_t>(), ntiles, s));
+    int32_t n_items = 0;
+    AZ_CUDA(cudaMemcpyAsync(&n_items, ioff.as<int32_t>() + ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AZ_CUDA(cudaStreamSynchronize(s));
-    AZ_TRY(L.active_tiles.alloc(sizeof(int32_t) * std::max(n_active, 1)));
-    AZ_TRY(launch_gs(compact_kernel, ntiles, s, aflag.as<int32_t>(), apos.as<int32_t>(), ntiles,
-                     L.active_tiles.as<int32_t>()));
-    max_kernel<<<1, 1024, 0, s>>>(tpadcnt.as<int32_t>(), ntiles, mx.as<int32_t>());
-    AZ_CUDA(cudaGetLastError());
-    max_kernel<<<1, 1024, 0, s>>>(scnt.as<int32_t>(), ntiles, mx.as<int32_t>() + 1);
-    AZ_CUDA(cudaGetLastError());
-    int32_t maxes[2];
-    AZ_CUDA(cudaMemcpyAsync(maxes, mx.p, sizeof(maxes), cudaMemcpyDeviceToHost, s));
-    AZ_CUDA(cudaStreamSynchronize(s));
+    AZ_TRY(chunks.alloc(sizeof(int32_t) * 3 * (size_t)std::max(n_items, 1)));
+    AZ_TRY(launch_gs(chunk_kernel, ntiles, s, L.tile_seg_ptr.as<int32_t>(), L.seg_ent_ptr.as<int32_t>(),
+                     L.seg_ent_ptr.as<int32_t>() + nseg, ntiles, kItemEntries, 1, icnt.as<int32_t>(),
+                     (const int32_t *)ioff.as<int32_t>(), chunks.as<int32_t>()));
 
-    if (maxes[0] > 65535)
-        return fail(AZ_EUNSUPPORTED, "a %dx%d tile holds %d matrix entries (limit 65535): use smaller tiles",
-                    th, tw, maxes[0]);
-
-    // per-tile records and descriptors
-    DevBuf rwords, roff;
-    AZ_TRY(rwords.alloc(sizeof(int32_t) * std::max(n_active, 1)));
-    AZ_TRY(roff.alloc(sizeof(int32_t) * (n_active + 1)));
-    AZ_TRY(launch_gs(rec_words_kernel, n_active, s, L.active_tiles.as<int32_t>(), n_active,
-                     L.tile_seg_ptr.as<int32_t>(), rwords.as<int32_t>()));
-    AZ_TRY(exclusive_scan_i32(rwords.as<int32_t>(), roff.as<int32_t>(), n_active, s));
+    // per-item records and descriptors, and the largest item
+    DevBuf rwords, roff, ient, iseg;
+    AZ_TRY(rwords.alloc(sizeof(int32_t) * std::max(n_items, 1)));
+    AZ_TRY(roff.alloc(sizeof(int32_t) * (n_items + 1)));
+    AZ_TRY(ient.alloc(sizeof(int32_t) * std::max(n_items, 1)));
+    AZ_TRY(iseg.alloc(sizeof(int32_t) * std::max(n_items, 1)));
+    AZ_TRY(launch_gs(rec_words_kernel, n_items, s, chunks.as<int32_t>(), n_items, rwords.as<int32_t>()));
+    AZ_TRY(exclusive_scan_i32(rwords.as<int32_t>(), roff.as<int32_t>(), n_items, s));
     int32_t rec_total = 0;
-    AZ_CUDA(cudaMemcpyAsync(&rec_total, roff.as<int32_t>() + n_active, sizeof(int32_t),
+    AZ_CUDA(cudaMemcpyAsync(&rec_total, roff.as<int32_t>() + n_items, sizeof(int32_t),
                             cudaMemcpyDeviceToHost, s));
-    max_kernel<<<1, 1024, 0, s>>>(rwords.as<int32_t>(), n_active, mx.as<int32_t>());
-    AZ_CUDA(cudaGetLastError());
-    int32_t max_rec = 0;
-    AZ_CUDA(cudaMemcpyAsync(&max_rec, mx.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AZ_CUDA(cudaStreamSynchronize(s));
     AZ_TRY(L.tile_rec.alloc(sizeof(int32_t) * std::max(rec_total, 4)));
-    AZ_TRY(L.tile_desc.alloc(sizeof(int32_t) * 8 * (size_t)std::max(n_active, 1)));
-    AZ_TRY(launch_gs(rec_fill_kernel, n_active, s, L.active_tiles.as<int32_t>(), n_active,
-                     L.tile_seg_ptr.as<int32_t>(), L.tile_ent_ptr.as<int32_t>(),
+    AZ_TRY(L.tile_desc.alloc(sizeof(int32_t) * 8 * (size_t)std::max(n_items, 1)));
+    AZ_TRY(launch_gs(rec_fill_kernel, n_items, s, chunks.as<int32_t>(), n_items,
                      L.seg_ent_ptr.as<int32_t>(), L.seg_ent_ptr.as<int32_t>() + nseg,
                      L.seg_slot.as<int32_t>(), roff.as<int32_t>(), L.tile_rec.as<int32_t>(),
-                     L.tile_desc.as<int32_t>()));
+                     L.tile_desc.as<int32_t>(), ient.as<int32_t>(), iseg.as<int32_t>()));
+    max_kernel<<<1, 1024, 0, s>>>(ient.as<int32_t>(), n_items, mx.as<int32_t>());
+    AZ_CUDA(cudaGetLastError());
+    max_kernel<<<1, 1024, 0, s>>>(iseg.as<int32_t>(), n_items, mx.as<int32_t>() + 1);
+    AZ_CUDA(cudaGetLastError());
+    max_kernel<<<1, 1024, 0, s>>>(rwords.as<int32_t>(), n_items, mx.as<int32_t>() + 2);
+    AZ_CUDA(cudaGetLastError());
+    int32_t maxes[3];
+    AZ_CUDA(cudaMemcpyAsync(maxes, mx.p, sizeof(maxes), cudaMemcpyDeviceToHost, s));
     AZ_CUDA(cudaStreamSynchronize(s));
+    if (maxes[0] > 65535)
+        return fail(AZ_EUNSUPPORTED, "a %dx%d tile item holds %d matrix entries (limit 65535): use smaller tiles",
+                    th, tw, maxes[0]);
+    // tile of every item (kept for accounting)
+    AZ_TRY(L.active_tiles.alloc(sizeof(int32_t) * std::max(n_items, 1)));
+    if (n_items > 0)
+        AZ_CUDA(cudaMemcpy2DAsync(L.active_tiles.p, sizeof(int32_t), chunks.p, 3 * sizeof(int32_t),
+                                  sizeof(int32_t), (size_t)n_items, cudaMemcpyDeviceToDevice, s));
+    AZ_CUDA(cudaStreamSynchronize(s));
+    const int32_t n_active = n_items;
+    const int32_t max_rec = maxes[2];
 
     L.th = th; L.tw = tw; L.srow = T.srow; L.ss = T.ss; L.ntx = T.ntx; L.nty = nty; L.ntiles = ntiles;
     L.n_active = n_active; L.nseg = nseg; L.padded_nnz = padded;

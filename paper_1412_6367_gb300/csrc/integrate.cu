@@ -1052,6 +1052,61 @@ __device__ __forceinline__ const Inst &inst_of_row(const Inst &single, const Ins
     return multi[lo];
 }
 
+// The value row_sum<float> computes, formed by one thread: the 32 lanes' strided Kahan sums
+// and the same lower-lane-left merge tree, each virtual lane's sum kept in registers.  For
+// rows with few slots (2D patterns: ~1-2 segments per row) this replaces a warp per row and
+// frame by a thread; the bits are the same.
+__device__ __forceinline__ Kahan kahan_one(float v) {
+    Kahan k{0.f, 0.f};
+    kahan_add(k, 1.f, v);
+    return k;
+}
+
+__device__ __forceinline__ float row_sum_thread(const float *p, int a, int b) {
+    // Up to four slots: the tree's only non-trivial merges (a merge with an empty lane's
+    // {+0, +0} changes no bit), in the tree's order.
+    const int n = b - a;
+    if (n <= 0) return 0.f;
+    if (n == 1) return kahan_value(kahan_one(p[a]));
+    if (n <= 4) {
+        Kahan x0 = kahan_one(p[a]), x1 = kahan_one(p[a + 1]);
+        if (n == 2) {
+            kahan_merge(x0, x1);
+            return kahan_value(x0);
+        }
+        kahan_merge(x0, kahan_one(p[a + 2]));       // lanes 0 and 2 at the pairs-of-two level
+        if (n == 4) kahan_merge(x1, kahan_one(p[a + 3]));
+        kahan_merge(x0, x1);
+        return kahan_value(x0);
+    }
+    Kahan v[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+        v[l].s = 0.f;
+        v[l].nc = 0.f;
+        for (int s = a + l; s < b; s += 32) kahan_add(v[l], 1.f, p[s]);
+    }
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1)
+#pragma unroll
+        for (int l = 0; l < m; ++l) kahan_merge(v[l], v[l + m]);
+    return kahan_value(v[0]);
+}
+
+// Frames-mode phase 2 with one thread per (row, frame), for rows of few slots.
+__global__ void phase2_frames_thread_kernel(const __grid_constant__ Inst d, int64_t n_jobs) {
+    for (int64_t job = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; job < n_jobs;
+         job += (int64_t)gridDim.x * blockDim.x) {
+        const int f = (int)(job / d.nrows), r = (int)(job - (int64_t)f * d.nrows);
+        const int a = d.row_slot_ptr[r], b = d.row_slot_ptr[r + 1];
+        const float S = row_sum_thread(static_cast<const float *>(d.partial) + (size_t)f * d.nseg, a, b);
+        const float N = d.norm[r];
+        const size_t o = (size_t)(d.frame_out0 + f) * d.nrows + r;
+        if (d.oS) static_cast<float *>(d.oS)[o] = S;
+        if (d.oI) static_cast<float *>(d.oI)[o] = N != 0.f ? __fdiv_rn(S, N) : 0.f;
+    }
+}
+
 template <class AT, int MODE>
 __global__ void phase2_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ multi,
                               int n_inst, int64_t n_jobs, int n_frames) {
@@ -1215,6 +1270,14 @@ template <class AT, int MODE>
 int run_phase2(const Inst &single, const Inst *multi, int n_inst, int64_t n_jobs, int n_frames,
                cudaStream_t s, Profiler *prof = nullptr) {
     if (n_jobs <= 0) return AZ_OK;
+    if (MODE == MODE_FRAMES && sizeof(AT) == 4 && !multi && (int64_t)single.nseg <= 8 * (int64_t)single.nrows) {
+        // few slots per row: a thread per (row, frame)
+        const int64_t blocks = std::min<int64_t>((n_jobs + 255) / 256, (int64_t)num_sms() * 16);
+        ProfScope ps(prof, 3, s);
+        phase2_frames_thread_kernel<<<(unsigned)blocks, 256, 0, s>>>(single, n_jobs);
+        AZ_CUDA(cudaGetLastError());
+        return AZ_OK;
+    }
     const int warps_per_block = 8;
     int64_t blocks = (n_jobs + warps_per_block - 1) / warps_per_block;
     blocks = std::min<int64_t>(blocks, (int64_t)num_sms() * 16);

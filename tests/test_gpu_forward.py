@@ -123,6 +123,29 @@ def test_batch_equals_single_frame():
         assert per <= 1e-5 and norm <= 1e-5
 
 
+def test_cake_batch_equals_single_frame():
+    """2D: the batched path (and its one-thread-per-row finalisation for rows of few
+    segments) gives the single-frame bits; N and C again on a second call (cached C)."""
+    w = small_workload(96, 128, split=2, npt=40, npt_azim=90, unit=0, seed=29, dtype="float32")
+    c = Case(w)
+    gpu = c.gpu_from_oracle_positions()
+    corr = c.corrections_dev()
+    frames = np.stack([synth.uniform_image(96, 128, seed=s, lo=0, hi=3000) for s in range(7)])
+    fd = to_dev(frames)
+    for call in range(2):
+        out = gpu.integrate_batch(fd, *corr)
+        for k in range(frames.shape[0]):
+            one = gpu.integrate(fd[k], *corr, precision="fp32")
+            assert torch.equal(out.I[k], one.I.reshape(-1)), (call, k)
+            assert torch.equal(out.sum_signal[k], one.sum_signal.reshape(-1))
+        assert torch.equal(out.sum_norm, one.sum_norm.reshape(-1))
+        assert torch.equal(out.count, one.count.reshape(-1))
+    ref = c.oracle(frames[4])
+    for got, r in zip((out.I[4], out.sum_signal[4], out.sum_norm, out.count), ref):
+        per, norm = rel_err(got.cpu().numpy(), r)
+        assert per <= 1e-5 and norm <= 1e-5
+
+
 @pytest.mark.parametrize("tile", [(16, 64), (32, 32), (64, 64), (16, 128), (8, 256)])
 @pytest.mark.parametrize("rpw", [1, 4, 32])
 def test_tunings_give_same_answer(tile, rpw):
