@@ -317,8 +317,14 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     out["stream_4096x2167x2070"] = {"frames_per_s": 256 / (ms / 1e3), "ms_per_4096": 16 * ms}
     del buf, fr, ig
 
-    # adjoint (image and flat-field gradients) on the Pilatus matrix, FP32 and FP64
+    # one Pilatus frame per call through the single-frame path (FP32 compensated)
     img, dark, flat, sa, pol = pilatus_inputs
+    for _ in range(3):
+        ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32")
+    ms = _event_ms(torch, lambda: ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32"), 20)
+    out["pilatus_single_frame_fp32"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
+
+    # adjoint (image and flat-field gradients) on the Pilatus matrix, FP32 and FP64
     for prec in ("fp32", "fp64"):
         res = ig_pilatus.integrate(img, dark, flat, sa, pol, precision=prec)
         gI = torch.ones_like(res.I)

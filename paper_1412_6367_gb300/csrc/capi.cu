@@ -230,6 +230,15 @@ static int integrate_common(const az_integrator *h, const void *image, int dtype
     if (two_d && h->npt_azim == 0) return fail(AZ_ESHAPE, "%s: integrator is 1D", who);
     if (!two_d && h->npt_azim != 0) return fail(AZ_ESHAPE, "%s: integrator is 2D", who);
     const_cast<az_integrator *>(h)->last_stream = (cudaStream_t)stream;
+    if (precision == AZ_PREC_FP32_COMP) {
+        // the batched machinery on a batch of one frame: the same arithmetic per frame as
+        // the single-frame kernel (which remains the path without the tensor-copy engine)
+        const int rc = forward_batch_one(const_cast<az_integrator *>(h), image, dtype, dark, flat, sa, pol,
+                                         static_cast<float *>(oI), static_cast<float *>(oS),
+                                         static_cast<float *>(oN), static_cast<float *>(oC),
+                                         (cudaStream_t)stream);
+        if (rc != AZ_EUNSUPPORTED) return rc;
+    }
     return forward_single(h, image, dtype, dark, flat, sa, pol, precision, oI, oS, oN, oC,
                           (cudaStream_t)stream);
 }

@@ -1460,7 +1460,9 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     FrGeom fg;
     // one or two frames of float values without a dark (the norm pass): one lane per
     // segment and frame, 32 / nf segments per warp
-    const bool small = nf <= 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr;
+    // one frame (any image type, with or without a dark), or two frames of float values
+    // without a dark (the norm pass): one lane per segment and frame
+    const bool small = nf == 1 || (nf == 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr);
     if (small) G = nf;
     else if (nf < G) G = nf <= 4 ? 4 : (nf <= 8 ? 8 : G);
     bool fits = fr_geom(h, G, ent_dark != nullptr, (nf + G - 1) / G, fg);
@@ -1483,7 +1485,7 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     TmaSet tm;
     AZ_TRY(make_maps(h, AZ_COPY_TMA, img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
     if (small)
-        return G == 1 ? fr_launch<1, AZ_DTYPE_F32, false>(a, fg, tm, s, &h->prof, prof_kind)
+        return G == 1 ? fr_launch_dt<1>(dtype, a, fg, tm, s, &h->prof, prof_kind)
                       : fr_launch<2, AZ_DTYPE_F32, false>(a, fg, tm, s, &h->prof, prof_kind);
     switch (G) {
         case 4: return fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof, prof_kind);
@@ -1711,6 +1713,17 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
         AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
     }
     return AZ_OK;
+}
+
+// One frame through the batched path (TMA engine only; AZ_EUNSUPPORTED, without error
+// text, otherwise).  The N pass needs two frames of partials.
+int forward_batch_one(az_integrator *h, const void *image, int dtype, const float *dark,
+                      const float *flat, const float *sa, const float *pol, float *oI, float *oS,
+                      float *oN, float *oC, cudaStream_t s) {
+    if (engine_for(h) != AZ_COPY_TMA || h->partial_bytes < 2 * sizeof(float) * (size_t)h->tl.nseg)
+        return AZ_EUNSUPPORTED;
+    AZ_TRY(batch_norm(h, flat, sa, pol, oN, oC, s));
+    return batch_frames(h, image, 1, dtype, dark, oI, oS, 0, s);
 }
 
 int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
