@@ -78,7 +78,7 @@ typedef struct {
     int64_t n_tiles, n_segments;
     int64_t device_bytes;      /* device memory owned by the integrator */
     int32_t copy_engine;       /* AZ_COPY_TMA or AZ_COPY_ASYNC */
-    int32_t reserved;
+    int32_t n_items;           /* work items of the forward: tiles, heavy ones cut in several */
 } az_info;
 
 /* ---- geometry (Sec. 3) ---------------------------------------------------------------- */
@@ -231,7 +231,8 @@ int az_integrate_noalloc(const az_integrator *h, const void *image_dev, int imag
  * device [n_frames][ny][nx]; the frame-independent sums N and C are formed once per call
  * and each matrix entry is applied to frames_per_pass frames per read.  FP32 compensated.
  * out_I, out_sum_signal: device float [n_frames][nrows] (either may be NULL);
- * out_sum_norm, out_count: device float [nrows] (may be NULL).
+ * out_sum_norm, out_count: device float [nrows] (may be NULL).  With n_frames == 0 only N and
+ * C are formed and frames_dev may be NULL.
  */
 int az_integrate_batch(az_integrator *h, const void *frames_dev, int n_frames,
                        int image_dtype, const float *dark, const float *flat,

@@ -37,7 +37,7 @@ class Info(ctypes.Structure):
                 ("rows_per_warp", ctypes.c_int32), ("frames_per_pass", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("copy_engine", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("n_items", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):

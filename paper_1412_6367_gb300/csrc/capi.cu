@@ -170,12 +170,14 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
     out->rows_per_warp = h->rows_per_warp; out->frames_per_pass = h->frames_per_pass;
     out->n_tiles = h->tl.ntiles; out->n_segments = h->tl.nseg;
     out->copy_engine = h->copy_engine;
+    out->n_items = h->tl.n_active;
     const DevBuf *bufs[] = {&h->csr_ptr, &h->csr_idx, &h->csr_w64, &h->csc_ptr, &h->csc_row,
                             &h->csc_w64, &h->csc_w32, &h->tl.tile_seg_ptr, &h->tl.tile_ent_ptr,
                             &h->tl.active_tiles, &h->tl.seg_ent_ptr, &h->tl.seg_slot,
                             &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_w32, &h->tl.ent_w64,
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
-                            &h->tl.tile_desc, &h->tl.tile_rec};
+                            &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
+                            &h->tl.norm_frames};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;
@@ -269,9 +271,11 @@ extern "C" int az_integrate_batch(az_integrator *h, const void *frames_dev, int 
                                   float *out_I, float *out_sum_signal, float *out_sum_norm,
                                   float *out_count, az_stream_t stream) {
     clear_error();
-    AZ_TRY(check_forward(h, frames_dev, image_dtype, dark, flat, solid_angle, polarization,
-                         "az_integrate_batch"));
     if (n_frames < 0) return fail(AZ_ESHAPE, "az_integrate_batch: n_frames < 0");
+    // with no frames only N and C are formed: the frames pointer may be NULL
+    static const uint32_t no_frames = 0;
+    AZ_TRY(check_forward(h, n_frames == 0 ? &no_frames : frames_dev, image_dtype, dark, flat,
+                         solid_angle, polarization, "az_integrate_batch"));
     h->last_stream = (cudaStream_t)stream;
     if (n_frames == 0 && !out_sum_norm && !out_count) return AZ_OK;
     return forward_batch(h, frames_dev, n_frames, image_dtype, dark, flat, solid_angle,
