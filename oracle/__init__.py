@@ -76,6 +76,7 @@ def _load():
         lib.orc_csr_copy.argtypes = [vp, vp, vp, vp]
         lib.orc_integrate.argtypes = [ctypes.c_int] + [vp] * 12
         lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 10
+        lib.orc_variance.argtypes = [ctypes.c_int] + [vp] * 5
         _lib = lib
         return lib
 
@@ -252,6 +253,16 @@ def backward(A: Csr, grad_I, I, N, solid_angle=None, polarization=None):
     lib.orc_backward(A.nrows, npix, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(g), _ptr(I), _ptr(N),
                      _ptr(sa), _ptr(pol), _ptr(gi), _ptr(gf))
     return gi, gf
+
+
+def variance(A: Csr, image):
+    """Propagated Poisson variance of each bin's signal sum, sum_p w^2 max(img_p, 0), float64."""
+    lib = _load()
+    img = _f64(np.asarray(image).reshape(-1))
+    V = np.empty(A.nrows)
+    ip, ix, dt = _csr_arrays(A)
+    lib.orc_variance(A.nrows, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(img), _ptr(V))
+    return V
 
 
 def radial_axis(A: Csr):

@@ -671,6 +671,26 @@ void orc_integrate(int nrows, const int64_t *indptr, const int32_t *indices, con
 }
 
 /*
+ * Propagated variance of the signal sum.  The paper states no error model; the reading used
+ * here is counting statistics: a pixel's counts have a Poisson variance equal to their value
+ * (clipped at 0), the dark current is a constant, and pixels are independent, so
+ * V_b = sum_p A_bp^2 max(img_p, 0), and the standard error of I_b is sqrt(V_b) / N_b.
+ */
+void orc_variance(int nrows, const int64_t *indptr, const int32_t *indices, const double *data,
+                  const double *img, double *V)
+{
+    for (int b = 0; b < nrows; ++b) {
+        double v = 0.0;
+        for (int64_t e = indptr[b]; e < indptr[b + 1]; ++e) {
+            double w = data[e];
+            double x = img[indices[e]];
+            v += w * w * (x > 0.0 ? x : 0.0);
+        }
+        V[b] = v;
+    }
+}
+
+/*
  * Adjoint of the forward with respect to the image and the flat field, for an upstream
  * gradient g_b = dL/dI_b:  dL/dimg_p = sum_b A_bp g_b / N_b,
  * dL/dflat_p = -Omega_p P_p sum_b A_bp g_b I_b / N_b (bins with N_b == 0 contribute 0).
