@@ -324,6 +324,13 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     ms = _event_ms(torch, lambda: ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32"), 20)
     out["pilatus_single_frame_fp32"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
 
+    # propagated Poisson variance of the bin sums, 64 Pilatus frames per call
+    fr64 = img.view(torch.int32).unsqueeze(0).expand(64, -1, -1).contiguous().view(torch.uint32)
+    ig_pilatus.variance(fr64)
+    ms = _event_ms(torch, lambda: ig_pilatus.variance(fr64), 5)
+    out["pilatus_variance_64_frames"] = {"us_per_frame": 1e3 * ms / 64}
+    del fr64
+
     # adjoint (image and flat-field gradients) on the Pilatus matrix, FP32 and FP64
     for prec in ("fp32", "fp64"):
         res = ig_pilatus.integrate(img, dark, flat, sa, pol, precision=prec)

@@ -241,6 +241,18 @@ int az_integrate_batch(az_integrator *h, const void *frames_dev, int n_frames,
                        az_stream_t stream);
 
 /*
+ * Propagated variance of each bin's signal sum under counting statistics (an extension:
+ * the paper states no error model): a pixel's counts have a Poisson variance equal to their
+ * value, clipped at 0, the dark current is a constant and pixels are independent, so
+ * V_b = sum_p A_bp^2 max(img_p, 0); the standard error of I_b is sqrt(V_b) / N_b.
+ * frames device [n_frames][ny][nx]; out_sum_variance device float [n_frames][nrows].
+ * FP32 compensated, through the batched kernel (tensor-copy engine; AZ_EUNSUPPORTED for
+ * tiles wider than 220 pixels).
+ */
+int az_integrate_variance(az_integrator *h, const void *frames_dev, int n_frames,
+                          int image_dtype, float *out_sum_variance, az_stream_t stream);
+
+/*
  * End-to-end form of az_integrate_batch on HOST buffers: frames_host [n_frames][ny][nx]
  * (pinned memory gives overlapped copies; pageable memory works but copies serialise),
  * outputs out_I_host / out_sum_signal_host [n_frames][nrows] float (either may be NULL).

@@ -274,6 +274,21 @@ class Integrator:
             _stream(dev)))
         return out
 
+    def variance(self, frames, out=None):
+        """Propagated Poisson variance of the bin sums, sum w^2 max(img, 0), of frames
+        [n, ny, nx] or of one frame [ny, nx] (az_integrate_variance, FP32 compensated).
+        Returns [n, nrows] (or [nrows] for one frame)."""
+        one = frames.dim() == 2
+        fr = frames.unsqueeze(0) if one else frames
+        n = fr.shape[0]
+        npix = self.info["ny"] * self.info["nx"]
+        if out is None:
+            out = torch.empty((n, self.nrows), dtype=torch.float32, device=fr.device)
+        check(self._lib.az_integrate_variance(self._h, _dev(fr, "frames", numel=n * npix), n,
+                                              image_dtype_code(fr), _dev(out, "out", torch.float32),
+                                              _stream(fr.device)))
+        return out[0] if one else out
+
     def integrate_batch_host(self, frames: torch.Tensor, dark=None, flat=None, solid_angle=None,
                              polarization=None, out_I=None, out_S=None):
         """End-to-end form on host buffers (az_integrate_batch_host): frames is a CPU tensor

@@ -283,6 +283,18 @@ extern "C" int az_integrate_batch(az_integrator *h, const void *frames_dev, int 
                          (cudaStream_t)stream);
 }
 
+extern "C" int az_integrate_variance(az_integrator *h, const void *frames_dev, int n_frames,
+                                     int image_dtype, float *out_sum_variance, az_stream_t stream) {
+    clear_error();
+    if (n_frames < 0) return fail(AZ_ESHAPE, "az_integrate_variance: n_frames < 0");
+    if (n_frames == 0) return AZ_OK;
+    AZ_TRY(check_forward(h, frames_dev, image_dtype, nullptr, nullptr, nullptr, nullptr,
+                         "az_integrate_variance"));
+    if (!out_sum_variance) return fail(AZ_EINVAL, "az_integrate_variance: NULL output");
+    h->last_stream = (cudaStream_t)stream;
+    return batch_variance(h, frames_dev, n_frames, image_dtype, out_sum_variance, (cudaStream_t)stream);
+}
+
 extern "C" int az_integrate_batch_host(az_integrator *h, const void *frames_host, int n_frames,
                                        int image_dtype, const float *dark, const float *flat,
                                        const float *solid_angle, const float *polarization,

@@ -189,6 +189,7 @@ int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const 
                   float *oN, float *oC, cudaStream_t s);
 int backward(const az_integrator *h, const void *g, const void *I, const void *N, const float *sa,
              const float *pol, int precision, void *g_img, void *g_flat, cudaStream_t s);
+int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float *oV, cudaStream_t s);
 int forward_batch_one(az_integrator *h, const void *image, int dtype, const float *dark,
                       const float *flat, const float *sa, const float *pol, float *oI, float *oS,
                       float *oN, float *oC, cudaStream_t s);

@@ -704,6 +704,9 @@ constexpr int kFrConsumers = 16;
 constexpr int kFrThreads = 32 * (1 + kFrConsumers);
 constexpr int kFrMaxStages = 8;
 constexpr int kFrMaxEbufs = 6;
+// What the frames kernel sums per entry: w (img), w (img - dark), or w^2 max(img, 0) (the
+// propagated Poisson variance of the signal sum).
+enum ValueMode { VM_PLAIN = 0, VM_DARK = 1, VM_VAR = 2 };
 constexpr uint32_t kFrStageHeader = 128;  // per plane stage: nimg, group, G plane offsets
 
 struct FrArgs {
@@ -715,6 +718,7 @@ struct FrArgs {
     float *partial;                       // [n_frames][nseg]
     int nseg, ny, nx, th, tw, srow, ss, ntx;
     int *status;
+    int var;                              // sum w^2 max(img, 0) instead of w img
 };
 
 struct FrGeom {
@@ -849,6 +853,11 @@ __device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
     f32x2 r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
@@ -866,7 +875,7 @@ __device__ __forceinline__ void kahan2_add(f32x2 &s, f32x2 &nc, f32x2 w, f32x2 v
 // entry stream of the tile's entry buffer, exactly as consume_serial does in frames mode (same
 // entry order, accumulator assignment and merge); accumulators (0, 1) and (2, 3) are stepped
 // as packed f32x2 pairs.
-template <int G, int DT, bool DK>
+template <int G, int DT, int VM>
 __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, const unsigned char *eb,
                                            const uint32_t *planes, const int *hdr, int *ctr) {
     constexpr int R = 32 / G;
@@ -906,14 +915,23 @@ __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, co
             v[1] = img_f32<DT>(P[l2.x >> 16]);
             v[2] = img_f32<DT>(P[l2.y & 0xffffu]);
             v[3] = img_f32<DT>(P[l2.y >> 16]);
+            if (VM == VM_VAR) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[j] = fmaxf(v[j], 0.f);
+            }
             f32x2 v01 = f2_pack(v[0], v[1]), v23 = f2_pack(v[2], v[3]);
-            if (DK) {
+            if (VM == VM_DARK) {
                 const float4 d4 = *reinterpret_cast<const float4 *>(D + qd);
                 v01 = f2_sub(v01, f2_pack(d4.x, d4.y));
                 v23 = f2_sub(v23, f2_pack(d4.z, d4.w));
             }
-            kahan2_add(s01, n01, f2_pack(w4.x, w4.y), v01);
-            kahan2_add(s23, n23, f2_pack(w4.z, w4.w), v23);
+            f32x2 w01 = f2_pack(w4.x, w4.y), w23 = f2_pack(w4.z, w4.w);
+            if (VM == VM_VAR) {
+                w01 = f2_mul(w01, w01);
+                w23 = f2_mul(w23, w23);
+            }
+            kahan2_add(s01, n01, w01, v01);
+            kahan2_add(s23, n23, w23, v23);
         }
         Kahan k[4];
         f2_unpack(s01, k[0].s, k[1].s);
@@ -930,7 +948,7 @@ __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, co
 // Bounded grace wait for copies this CTA issued before giving up (every wait is bounded).
 __device__ __forceinline__ void fr_drain(uint64_t *bar, uint32_t parity) { (void)mbar_wait_bounded(bar, parity); }
 
-template <int G, int DT, bool DK>
+template <int G, int DT, int VM>
 __global__ void __launch_bounds__(kFrThreads, 1)
 frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant__ TmaSet tm) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1015,7 +1033,7 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
                     stop = true;
                     break;
                 }
-                fr_consume<G, DT, DK>(a, fg, ebp, reinterpret_cast<const uint32_t *>(pst + (size_t)s * fg.pstage_bytes),
+                fr_consume<G, DT, VM>(a, fg, ebp, reinterpret_cast<const uint32_t *>(pst + (size_t)s * fg.pstage_bytes),
                                       hdrs + s * (kFrStageHeader / 4), &ctr[s]);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&pempty[s]);
@@ -1420,12 +1438,12 @@ uint32_t fr_smem(const FrGeom &fg) {
            kFrFixedBytes;
 }
 
-template <int G, int DT, bool DK>
+template <int G, int DT, int VM>
 int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s, Profiler *prof,
               int prof_kind) {
     if (a.n_tiles <= 0) return AZ_OK;
     const uint32_t smem = fr_smem(fg);
-    auto kern = frames_kernel<G, DT, DK>;
+    auto kern = frames_kernel<G, DT, VM>;
     AZ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = std::min(a.n_tiles, num_sms());
     {
@@ -1439,14 +1457,20 @@ int fr_launch(const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t 
 template <int G>
 int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm, cudaStream_t s,
                  Profiler *prof, int kind) {
-    const bool dk = a.ent_dark != nullptr;
+    const int vm = a.var ? VM_VAR : (a.ent_dark != nullptr ? VM_DARK : VM_PLAIN);
     switch (dtype) {
         case AZ_DTYPE_F32:
-            return dk ? fr_launch<G, AZ_DTYPE_F32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_F32, false>(a, fg, tm, s, prof, kind);
+            return vm == VM_DARK ? fr_launch<G, AZ_DTYPE_F32, VM_DARK>(a, fg, tm, s, prof, kind)
+                 : vm == VM_VAR  ? fr_launch<G, AZ_DTYPE_F32, VM_VAR>(a, fg, tm, s, prof, kind)
+                                 : fr_launch<G, AZ_DTYPE_F32, VM_PLAIN>(a, fg, tm, s, prof, kind);
         case AZ_DTYPE_U32:
-            return dk ? fr_launch<G, AZ_DTYPE_U32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_U32, false>(a, fg, tm, s, prof, kind);
+            return vm == VM_DARK ? fr_launch<G, AZ_DTYPE_U32, VM_DARK>(a, fg, tm, s, prof, kind)
+                 : vm == VM_VAR  ? fr_launch<G, AZ_DTYPE_U32, VM_VAR>(a, fg, tm, s, prof, kind)
+                                 : fr_launch<G, AZ_DTYPE_U32, VM_PLAIN>(a, fg, tm, s, prof, kind);
         default:
-            return dk ? fr_launch<G, AZ_DTYPE_I32, true>(a, fg, tm, s, prof, kind) : fr_launch<G, AZ_DTYPE_I32, false>(a, fg, tm, s, prof, kind);
+            return vm == VM_DARK ? fr_launch<G, AZ_DTYPE_I32, VM_DARK>(a, fg, tm, s, prof, kind)
+                 : vm == VM_VAR  ? fr_launch<G, AZ_DTYPE_I32, VM_VAR>(a, fg, tm, s, prof, kind)
+                                 : fr_launch<G, AZ_DTYPE_I32, VM_PLAIN>(a, fg, tm, s, prof, kind);
     }
 }
 
@@ -1454,7 +1478,7 @@ int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm,
 // per-segment partials [nf][nseg] in h->partial.  Returns AZ_EUNSUPPORTED (without error
 // text) when the TMA engine or the shared memory it needs is not available.
 int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float *ent_dark,
-              int prof_kind, cudaStream_t s) {
+              int prof_kind, cudaStream_t s, bool var = false) {
     if (engine_for(h) != AZ_COPY_TMA) return AZ_EUNSUPPORTED;
     int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
     FrGeom fg;
@@ -1462,7 +1486,7 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     // segment and frame, 32 / nf segments per warp
     // one frame (any image type, with or without a dark), or two frames of float values
     // without a dark (the norm pass): one lane per segment and frame
-    const bool small = nf == 1 || (nf == 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr);
+    const bool small = nf == 1 || (nf == 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr && !var);
     if (small) G = nf;
     else if (nf < G) G = nf <= 4 ? 4 : (nf <= 8 ? 8 : G);
     bool fits = fr_geom(h, G, ent_dark != nullptr, (nf + G - 1) / G, fg);
@@ -1478,6 +1502,7 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     a.tile_desc = L.tile_desc.as<int32_t>(); a.tile_rec = L.tile_rec.as<int32_t>();
     a.ent_loc = L.ent_loc.as<uint16_t>(); a.ent_w = L.ent_w32.as<float>();
     a.ent_dark = ent_dark;
+    a.var = var ? 1 : 0;
     a.partial = h->partial.as<float>();
     a.nseg = L.nseg; a.ny = h->ny; a.nx = h->nx; a.th = L.th; a.tw = L.tw; a.srow = L.srow;
     a.ss = L.ss; a.ntx = L.ntx;
@@ -1486,7 +1511,7 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     AZ_TRY(make_maps(h, AZ_COPY_TMA, img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
     if (small)
         return G == 1 ? fr_launch_dt<1>(dtype, a, fg, tm, s, &h->prof, prof_kind)
-                      : fr_launch<2, AZ_DTYPE_F32, false>(a, fg, tm, s, &h->prof, prof_kind);
+                      : fr_launch<2, AZ_DTYPE_F32, VM_PLAIN>(a, fg, tm, s, &h->prof, prof_kind);
     switch (G) {
         case 4: return fr_launch_dt<4>(dtype, a, fg, tm, s, &h->prof, prof_kind);
         case 8: return fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof, prof_kind);
@@ -1710,6 +1735,28 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
             case 16: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 16>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
             default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 32>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
         }
+        AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
+    }
+    return AZ_OK;
+}
+
+// Propagated variance of the signal sums, V = sum w^2 max(img, 0), for n frames through the
+// frames kernel (chunks of up to 64 frames), written to oV [n][nrows].
+int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float *oV, cudaStream_t s) {
+    if (engine_for(h) != AZ_COPY_TMA)
+        return fail(AZ_EUNSUPPORTED, "az_integrate_variance: needs the tensor-copy engine (tiles up to 220 pixels wide)");
+    const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(h->tl.nseg, 1)));
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+    for (int f0 = 0; f0 < n; f0 += chunk) {
+        const int nf = std::min(chunk, n - f0);
+        Inst d = make_inst(h, false);
+        d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
+        const int rc = frames_v3(h, d.img, nf, dtype, nullptr, 0, s, true);
+        if (rc == AZ_EUNSUPPORTED)
+            return fail(AZ_EUNSUPPORTED, "az_integrate_variance: the tiles do not fit in shared memory");
+        AZ_TRY(rc);
+        d.n_frames = nf;
+        d.oI = nullptr; d.oS = oV; d.frame_out0 = f0;
         AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
     }
     return AZ_OK;
