@@ -77,6 +77,7 @@ def _load():
         lib.orc_integrate.argtypes = [ctypes.c_int] + [vp] * 12
         lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 10
         lib.orc_variance.argtypes = [ctypes.c_int] + [vp] * 5
+        lib.orc_integrate_pixelnorm.argtypes = [ctypes.c_int] + [vp] * 11
         _lib = lib
         return lib
 
@@ -253,6 +254,20 @@ def backward(A: Csr, grad_I, I, N, solid_angle=None, polarization=None):
     lib.orc_backward(A.nrows, npix, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(g), _ptr(I), _ptr(N),
                      _ptr(sa), _ptr(pol), _ptr(gi), _ptr(gf))
     return gi, gf
+
+
+def integrate_pixelnorm(A: Csr, image, dark=None, flat=None, solid_angle=None, polarization=None):
+    """The paper's per-pixel-corrected form: (I, U, C) with U = sum w (img - dark) / (flat
+    solid_angle polarisation), C = sum w, I = U / C; float64."""
+    lib = _load()
+    img = _f64(np.asarray(image).reshape(-1))
+    dark, flat, sa, pol = (None if a is None else _f64(np.asarray(a).reshape(-1))
+                           for a in (dark, flat, solid_angle, polarization))
+    I, U, C = (np.empty(A.nrows) for _ in range(3))
+    ip, ix, dt = _csr_arrays(A)
+    lib.orc_integrate_pixelnorm(A.nrows, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(img), _ptr(dark),
+                                _ptr(flat), _ptr(sa), _ptr(pol), _ptr(I), _ptr(U), _ptr(C))
+    return I, U, C
 
 
 def variance(A: Csr, image):

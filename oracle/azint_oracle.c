@@ -671,6 +671,33 @@ void orc_integrate(int nrows, const int64_t *indptr, const int32_t *indices, con
 }
 
 /*
+ * The paper's own normalisation (Sec. 6.4, the correction pass then the integration, whose
+ * outputs are the ratio of two histograms): each pixel is corrected first,
+ * c_p = (img_p - dark_p) / (flat_p Omega_p P_p), then U_b = sum_p A_bp c_p, C_b = sum_p A_bp
+ * and I_b = U_b / C_b (0 where C_b = 0).  Absent corrections are 0 (dark) and 1.
+ */
+void orc_integrate_pixelnorm(int nrows, const int64_t *indptr, const int32_t *indices,
+                             const double *data, const double *img, const double *dark,
+                             const double *flat, const double *sa, const double *pol, double *I,
+                             double *U, double *C)
+{
+    for (int b = 0; b < nrows; ++b) {
+        double u = 0.0, c = 0.0;
+        for (int64_t e = indptr[b]; e < indptr[b + 1]; ++e) {
+            int32_t p = indices[e];
+            double w = data[e];
+            double v = img[p] - (dark ? dark[p] : 0.0);
+            double nrm = (flat ? flat[p] : 1.0) * (sa ? sa[p] : 1.0) * (pol ? pol[p] : 1.0);
+            u += w * (v / nrm);
+            c += w;
+        }
+        U[b] = u;
+        C[b] = c;
+        I[b] = (c != 0.0) ? u / c : 0.0;
+    }
+}
+
+/*
  * Propagated variance of the signal sum.  The paper states no error model; the reading used
  * here is counting statistics: a pixel's counts have a Poisson variance equal to their value
  * (clipped at 0), the dark current is a constant, and pixels are independent, so
