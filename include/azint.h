@@ -241,6 +241,24 @@ int az_integrate_batch(az_integrator *h, const void *frames_dev, int n_frames,
                        az_stream_t stream);
 
 /*
+ * The paper's own normalisation (Sec. 6.4: a correction pass, then the integration, whose
+ * result is a ratio of two histograms): each pixel is corrected first,
+ * c = (img - dark) / (flat * solid_angle * polarization), then U = sum w c, C = sum w and
+ * I = U / C (0 where C = 0).  frames device [n_frames][ny][nx]; corrections as in
+ * az_integrate_batch (NULL = absent); out_I, out_sum_corrected device float
+ * [n_frames][nrows], out_count device float [nrows] (any may be NULL).  FP32 compensated;
+ * computed with the weights divided by each pixel's flat * solid_angle * polarization once
+ * per call.  Through the batched kernel (tensor-copy engine; AZ_EUNSUPPORTED for tiles
+ * wider than 220 pixels).  With no flat, solid angle or polarisation the result equals
+ * az_integrate_batch's I and S bit for bit.
+ */
+int az_integrate_batch_pixelnorm(az_integrator *h, const void *frames_dev, int n_frames,
+                                 int image_dtype, const float *dark, const float *flat,
+                                 const float *solid_angle, const float *polarization,
+                                 float *out_I, float *out_sum_corrected, float *out_count,
+                                 az_stream_t stream);
+
+/*
  * Propagated variance of each bin's signal sum under counting statistics (an extension:
  * the paper states no error model): a pixel's counts have a Poisson variance equal to their
  * value, clipped at 0, the dark current is a constant and pixels are independent, so

@@ -74,6 +74,7 @@ SIGNATURES = {
     "az_integrate_batch": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_batch_host": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_variance": ([vp, vp, i32, i32, vp, vp], i32),
+    "az_integrate_batch_pixelnorm": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_backward": ([vp, vp, vp, vp, vp, vp, i32, vp, vp, vp], i32),
     "az_multi_create": ([PP, i32, PP, i32, PP, PP, PP, PP, PP, PP, PP, PP, PP], i32),
     "az_multi_launch": ([vp, i32, vp], i32),

@@ -274,6 +274,26 @@ class Integrator:
             _stream(dev)))
         return out
 
+    def integrate_pixelnorm(self, frames, dark=None, flat=None, solid_angle=None, polarization=None):
+        """The paper's per-pixel-corrected form (az_integrate_batch_pixelnorm) for frames
+        [n, ny, nx] or one frame [ny, nx]: returns (I, U, C) with U = sum w (img - dark) /
+        (flat solid_angle polarization), C = sum w, I = U / C."""
+        one = frames.dim() == 2
+        fr = frames.unsqueeze(0) if one else frames
+        n = fr.shape[0]
+        npix = self.info["ny"] * self.info["nx"]
+        dev = fr.device
+        I = torch.empty((n, self.nrows), dtype=torch.float32, device=dev)
+        U = torch.empty((n, self.nrows), dtype=torch.float32, device=dev)
+        C = torch.empty(self.nrows, dtype=torch.float32, device=dev)
+        check(self._lib.az_integrate_batch_pixelnorm(
+            self._h, _dev(fr, "frames", numel=n * npix), n, image_dtype_code(fr),
+            *self._corr(dark, flat, solid_angle, polarization), _dev(I, "I", torch.float32),
+            _dev(U, "U", torch.float32), _dev(C, "C", torch.float32), _stream(dev)))
+        if one:
+            I, U = I[0], U[0]
+        return I, U, C
+
     def variance(self, frames, out=None):
         """Propagated Poisson variance of the bin sums, sum w^2 max(img, 0), of frames
         [n, ny, nx] or of one frame [ny, nx] (az_integrate_variance, FP32 compensated).

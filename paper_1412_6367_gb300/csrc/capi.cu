@@ -177,7 +177,7 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
                             &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_w32, &h->tl.ent_w64,
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
                             &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
-                            &h->tl.norm_frames};
+                            &h->tl.norm_frames, &h->tl.ent_wnorm};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;
@@ -281,6 +281,21 @@ extern "C" int az_integrate_batch(az_integrator *h, const void *frames_dev, int 
     return forward_batch(h, frames_dev, n_frames, image_dtype, dark, flat, solid_angle,
                          polarization, out_I, out_sum_signal, out_sum_norm, out_count,
                          (cudaStream_t)stream);
+}
+
+extern "C" int az_integrate_batch_pixelnorm(az_integrator *h, const void *frames_dev, int n_frames,
+                                            int image_dtype, const float *dark, const float *flat,
+                                            const float *solid_angle, const float *polarization,
+                                            float *out_I, float *out_sum_corrected, float *out_count,
+                                            az_stream_t stream) {
+    clear_error();
+    if (n_frames < 0) return fail(AZ_ESHAPE, "az_integrate_batch_pixelnorm: n_frames < 0");
+    static const uint32_t no_frames = 0;
+    AZ_TRY(check_forward(h, n_frames == 0 ? &no_frames : frames_dev, image_dtype, dark, flat,
+                         solid_angle, polarization, "az_integrate_batch_pixelnorm"));
+    h->last_stream = (cudaStream_t)stream;
+    return batch_pixelnorm(h, frames_dev, n_frames, image_dtype, dark, flat, solid_angle, polarization,
+                           out_I, out_sum_corrected, out_count, (cudaStream_t)stream);
 }
 
 extern "C" int az_integrate_variance(az_integrator *h, const void *frames_dev, int n_frames,

@@ -97,6 +97,7 @@ struct TiledLayout {
     DevBuf ent_pix;         // int32  [padded_nnz] (pixel of the entry; -1 for padding)
     DevBuf ent_dark;        // float  [padded_nnz] (dark of the entry's pixel, per batch call)
     DevBuf norm_frames;     // float  [2][ny][nx]: flat * solid angle * polarisation, then ones
+    DevBuf ent_wnorm;       // float  [padded_nnz]: weight / (flat * solid angle * polarisation)
     // Per active tile: a 32-byte descriptor {tile, record offset (words), record words,
     // entry offset, padded entry count, segment count, 0, 0} and a 16-byte aligned record
     // {tile, ns, entry offset, entry count, slot[ns], uint16 start[ns + 1]} that the forward
@@ -190,6 +191,9 @@ int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const 
 int backward(const az_integrator *h, const void *g, const void *I, const void *N, const float *sa,
              const float *pol, int precision, void *g_img, void *g_flat, cudaStream_t s);
 int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float *oV, cudaStream_t s);
+int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
+                    const float *flat, const float *sa, const float *pol, float *oI, float *oU,
+                    float *oC, cudaStream_t s);
 int forward_batch_one(az_integrator *h, const void *image, int dtype, const float *dark,
                       const float *flat, const float *sa, const float *pol, float *oI, float *oS,
                       float *oN, float *oC, cudaStream_t s);

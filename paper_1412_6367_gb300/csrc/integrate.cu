@@ -1478,7 +1478,7 @@ int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm,
 // per-segment partials [nf][nseg] in h->partial.  Returns AZ_EUNSUPPORTED (without error
 // text) when the TMA engine or the shared memory it needs is not available.
 int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float *ent_dark,
-              int prof_kind, cudaStream_t s, bool var = false) {
+              int prof_kind, cudaStream_t s, bool var = false, const float *ent_weights = nullptr) {
     if (engine_for(h) != AZ_COPY_TMA) return AZ_EUNSUPPORTED;
     int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
     FrGeom fg;
@@ -1500,7 +1500,8 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     a.img = static_cast<const char *>(img);
     a.n_frames = nf; a.n_groups = (nf + G - 1) / G; a.n_tiles = L.n_active;
     a.tile_desc = L.tile_desc.as<int32_t>(); a.tile_rec = L.tile_rec.as<int32_t>();
-    a.ent_loc = L.ent_loc.as<uint16_t>(); a.ent_w = L.ent_w32.as<float>();
+    a.ent_loc = L.ent_loc.as<uint16_t>();
+    a.ent_w = ent_weights ? ent_weights : L.ent_w32.as<float>();
     a.ent_dark = ent_dark;
     a.var = var ? 1 : 0;
     a.partial = h->partial.as<float>();
@@ -1530,6 +1531,17 @@ __global__ void norm_pixels_kernel(const float *__restrict__ flat, const float *
         if (sa) v = __fmul_rn(v, sa[p]);
         if (pol) v = __fmul_rn(v, pol[p]);
         out[p] = v;
+    }
+}
+
+// Weight of each entry divided by its pixel's flat * solid angle * polarisation (0 for
+// padding entries): the weights of the per-pixel-corrected form.
+__global__ void gather_wnorm_kernel(const int32_t *__restrict__ pix, const float *__restrict__ w,
+                                    const float *__restrict__ npx, int64_t n, float *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = pix[e];
+        out[e] = p >= 0 ? __fdiv_rn(w[e], npx[p]) : 0.f;
     }
 }
 
@@ -1736,6 +1748,68 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
             default: AZ_TRY((run_phase1_dt<float, float, MODE_FRAMES, 32>(dtype, eng, d, nullptr, 1, d.n_items, sg, tm, s, &h->prof))); break;
         }
         AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
+    }
+    return AZ_OK;
+}
+
+// The paper's per-pixel-corrected form for n frames: U = sum (w / (flat Omega P)) (img - dark)
+// and I = U / C, C = sum w (kept per layout).  Through the frames kernel with the weights
+// divided by each pixel's normalisation once per call.
+int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
+                    const float *flat, const float *sa, const float *pol, float *oI, float *oU,
+                    float *oC, cudaStream_t s) {
+    if (engine_for(h) != AZ_COPY_TMA || h->partial_bytes < 2 * sizeof(float) * (size_t)h->tl.nseg)
+        return fail(AZ_EUNSUPPORTED, "az_integrate_batch_pixelnorm: needs the tensor-copy engine (tiles up to 220 pixels wide)");
+    TiledLayout &L = h->tl;
+    const int64_t npix = (int64_t)h->ny * h->nx;
+    const int nrows = h->nrows;
+    // C (and, incidentally, N = C) for the current layout
+    if (!h->count_ready) AZ_TRY(batch_norm(h, nullptr, nullptr, nullptr, nullptr, nullptr, s));
+    const float *Cdev = h->norm.as<float>() + nrows;
+    if (oC) AZ_CUDA(cudaMemcpyAsync(oC, Cdev, sizeof(float) * nrows, cudaMemcpyDeviceToDevice, s));
+    if (n == 0) return AZ_OK;
+    // per-pixel normalisation, per-entry corrected weights and darks
+    const int64_t pblocks = std::min<int64_t>((npix + 255) / 256, (int64_t)num_sms() * 8);
+    const int64_t eblocks = std::max<int64_t>(1, std::min<int64_t>((L.padded_nnz + 255) / 256, (int64_t)num_sms() * 8));
+    if (L.norm_frames.bytes < 2 * sizeof(float) * (size_t)npix) {
+        AZ_TRY(L.norm_frames.alloc(2 * sizeof(float) * (size_t)npix));
+        fill_f32_kernel<<<(unsigned)pblocks, 256, 0, s>>>(L.norm_frames.as<float>() + npix, npix, 1.f);
+        AZ_CUDA(cudaGetLastError());
+    }
+    if (L.ent_wnorm.bytes < sizeof(float) * (size_t)L.padded_nnz)
+        AZ_TRY(L.ent_wnorm.alloc(sizeof(float) * (size_t)L.padded_nnz));
+    {
+        ProfScope ps(&h->prof, 4, s);
+        norm_pixels_kernel<<<(unsigned)pblocks, 256, 0, s>>>(flat, sa, pol, npix, L.norm_frames.as<float>());
+        gather_wnorm_kernel<<<(unsigned)eblocks, 256, 0, s>>>(L.ent_pix.as<int32_t>(), L.ent_w32.as<float>(),
+                                                              L.norm_frames.as<float>(), L.padded_nnz,
+                                                              L.ent_wnorm.as<float>());
+        AZ_CUDA(cudaGetLastError());
+    }
+    const float *ent_dk = nullptr;
+    if (dark) {
+        if (L.ent_dark.bytes < sizeof(float) * (size_t)L.padded_nnz)
+            AZ_TRY(L.ent_dark.alloc(sizeof(float) * (size_t)L.padded_nnz));
+        ProfScope ps(&h->prof, 4, s);
+        gather_dark_kernel<<<(unsigned)eblocks, 256, 0, s>>>(L.ent_pix.as<int32_t>(), dark, L.padded_nnz,
+                                                             L.ent_dark.as<float>());
+        AZ_CUDA(cudaGetLastError());
+        ent_dk = L.ent_dark.as<float>();
+    }
+    const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(L.nseg, 1)));
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+    for (int f0 = 0; f0 < n; f0 += chunk) {
+        const int nf = std::min(chunk, n - f0);
+        Inst d = make_inst(h, false);
+        d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
+        const int rc = frames_v3(h, d.img, nf, dtype, ent_dk, 0, s, false, L.ent_wnorm.as<float>());
+        if (rc == AZ_EUNSUPPORTED)
+            return fail(AZ_EUNSUPPORTED, "az_integrate_batch_pixelnorm: the tiles do not fit in shared memory");
+        AZ_TRY(rc);
+        d.n_frames = nf;
+        d.norm = const_cast<float *>(Cdev);  // I = U / C
+        d.oI = oI; d.oS = oU; d.frame_out0 = f0;
+        AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * nrows, nf, s, &h->prof)));
     }
     return AZ_OK;
 }
