@@ -63,6 +63,7 @@ struct Inst {
     int *status;
     const int32_t *tile_desc, *tile_rec;  // per active tile: descriptor [8] and record
     const float *ent_dark;                // frames pass: dark of each entry's pixel (or NULL)
+    const CUtensorMap *maps;              // many-instance launch: this instance's [5][4] maps
 };
 
 struct StageGeom {
@@ -263,7 +264,7 @@ __device__ void produce(const Inst &d, const TmaSet &tm, int64_t local, const Ti
                 const int x = c0 - 4 * (flag + (pl & 3));
                 uint32_t *dst = planes + (size_t)pl * pw + (size_t)sl * d.ss;
                 const int y = (int)((g0 + sl - k) >> 2);
-                const CUtensorMap *map = &tm.m[kind][k];
+                const CUtensorMap *map = d.maps ? d.maps + 4 * kind + k : &tm.m[kind][k];
                 asm volatile(
                     "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
                     " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
@@ -1860,6 +1861,7 @@ int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const 
 struct MultiPlan {
     std::vector<Inst> host;
     DevBuf dev;
+    DevBuf maps;  // TMA engine: n TmaSets, one per instance, read by the producers
     int n = 0;
     int dtype = 0, engine = 0;
     int64_t n_items = 0, n_rows = 0;
@@ -1878,7 +1880,28 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
     P->dtype = dtype;
     int64_t items = 0, rows = 0;
     uint32_t pw = 0, ecap = 0, rw = 0;
-    P->engine = AZ_COPY_ASYNC;  // one launch over many arrays: no per-array tensor maps
+    // The TMA engine when every instance can use it: each instance's tensor maps then live in
+    // device memory (a launch parameter holds one set only) and the producers read them there.
+    P->engine = AZ_COPY_TMA;
+    for (int k = 0; k < n; ++k)
+        if (engine_for(hs[k]) != AZ_COPY_TMA) P->engine = AZ_COPY_ASYNC;
+    std::vector<TmaSet> maps;
+    if (P->engine == AZ_COPY_TMA) {
+        maps.resize((size_t)n);
+        int rc = P->maps.alloc(sizeof(TmaSet) * (size_t)n);
+        for (int k = 0; k < n && rc == AZ_OK; ++k)
+            rc = make_maps(hs[k], AZ_COPY_TMA, images[k], hs[k]->ny, darks ? darks[k] : nullptr,
+                           flats ? flats[k] : nullptr, sas ? sas[k] : nullptr, pols ? pols[k] : nullptr,
+                           maps[(size_t)k]);
+        if (rc == AZ_OK) {
+            cudaError_t e = cudaMemcpy(P->maps.p, maps.data(), sizeof(TmaSet) * (size_t)n, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) rc = fail(AZ_ECUDA, "az_multi_create: %s", cudaGetErrorString(e));
+        }
+        if (rc != AZ_OK) {
+            delete P;
+            return rc;
+        }
+    }
     int planes = 0;
     for (int k = 0; k < n; ++k) {
         const az_integrator *h = hs[k];
@@ -1892,6 +1915,7 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
         d.oS = oS ? oS[k] : nullptr;
         d.oN = oN ? oN[k] : nullptr;
         d.oC = oC ? oC[k] : nullptr;
+        if (P->engine == AZ_COPY_TMA) d.maps = &P->maps.as<TmaSet>()[k].m[0][0];
         d.item_begin = items;
         d.row_begin = rows;
         items += d.n_items;
@@ -1924,7 +1948,7 @@ int multi_create(az_integrator *const *hs, int n, const void *const *images, int
 int multi_enqueue(void *plan, cudaStream_t s) {
     MultiPlan *P = static_cast<MultiPlan *>(plan);
     const Inst *dev = P->dev.as<Inst>();
-    static TmaSet no_maps;  // zero: the cp.async engine does not read tensor maps
+    static TmaSet no_maps;  // zero: the producers read each instance's maps from Inst::maps
     AZ_TRY((run_phase1_dt<float, float, MODE_SINGLE, 1>(P->dtype, P->engine, P->host[0], dev, P->n, P->n_items, P->sg, no_maps, s)));
     AZ_TRY((run_phase2<float, MODE_SINGLE>(P->host[0], dev, P->n, P->n_rows, 1, s)));
     return AZ_OK;
