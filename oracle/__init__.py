@@ -78,6 +78,10 @@ def _load():
         lib.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 10
         lib.orc_variance.argtypes = [ctypes.c_int] + [vp] * 5
         lib.orc_integrate_pixelnorm.argtypes = [ctypes.c_int] + [vp] * 11
+        lib.orc_lut_width.argtypes = [ctypes.c_int, vp]
+        lib.orc_lut_width.restype = ctypes.c_int64
+        lib.orc_lut_from_csr.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int64, vp, vp]
+        lib.orc_integrate_lut.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 11
         _lib = lib
         return lib
 
@@ -278,6 +282,42 @@ def variance(A: Csr, image):
     ip, ix, dt = _csr_arrays(A)
     lib.orc_variance(A.nrows, _ptr(ip), _ptr(ix), _ptr(dt), _ptr(img), _ptr(V))
     return V
+
+
+def lut_from_csr_arrays(indptr, indices, data):
+    """The look-up table (Sec. 5.2) of a CSR matrix given as arrays: (idx int32, coef
+    float64), both [nrows][width], width = the longest row; each row holds its entries in
+    column order, then padding pairs (-1, 0.0)."""
+    lib = _load()
+    ip = np.ascontiguousarray(indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(indices, dtype=np.int32)
+    dt = np.ascontiguousarray(data, dtype=np.float64)
+    nrows = len(ip) - 1
+    width = int(lib.orc_lut_width(nrows, _ptr(ip)))
+    idx = np.empty((nrows, width), np.int32)
+    coef = np.empty((nrows, width), np.float64)
+    lib.orc_lut_from_csr(nrows, _ptr(ip), _ptr(ix), _ptr(dt), width, _ptr(idx), _ptr(coef))
+    return idx, coef
+
+
+def lut_from_csr(A: Csr):
+    """The look-up table of the oracle's matrix A (see lut_from_csr_arrays)."""
+    return lut_from_csr_arrays(*_csr_arrays(A))
+
+
+def integrate_lut(idx, coef, image, dark=None, flat=None, solid_angle=None, polarization=None):
+    """(I, S, N, C) per bin in float64 through a look-up table [nrows][width]."""
+    lib = _load()
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    nrows, width = idx.shape
+    img = _f64(np.asarray(image).reshape(-1))
+    dark, flat, sa, pol = (None if a is None else _f64(np.asarray(a).reshape(-1))
+                           for a in (dark, flat, solid_angle, polarization))
+    I, S, N, C = (np.empty(nrows) for _ in range(4))
+    lib.orc_integrate_lut(nrows, width, _ptr(idx), _ptr(coef), _ptr(img), _ptr(dark), _ptr(flat),
+                          _ptr(sa), _ptr(pol), _ptr(I), _ptr(S), _ptr(N), _ptr(C))
+    return I, S, N, C
 
 
 def radial_axis(A: Csr):

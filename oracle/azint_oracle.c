@@ -745,3 +745,61 @@ void orc_backward(int nrows, int64_t npix, const int64_t *indptr, const int32_t 
             g_flat[p] = -(sa ? sa[p] : 1.0) * (pol ? pol[p] : 1.0) * (acc ? acc[p] : 0.0);
     free(acc);
 }
+
+/*
+ * Look-up-table layout of the matrix (Sec. 5.2, "scatter to gather"): for every output bin,
+ * the pixels it takes its value from, as (pixel index, coefficient) pairs.  Every bin gets
+ * the same number of slots, `width` = the largest number of entries in any bin; bin b's
+ * slots hold its matrix row in column order, then padding pairs (index -1, coefficient 0).
+ * Row-major: slot k of bin b is element b * width + k.
+ */
+int64_t orc_lut_width(int nrows, const int64_t *indptr)
+{
+    int64_t w = 0;
+    for (int b = 0; b < nrows; ++b)
+        if (indptr[b + 1] - indptr[b] > w) w = indptr[b + 1] - indptr[b];
+    return w;
+}
+
+void orc_lut_from_csr(int nrows, const int64_t *indptr, const int32_t *indices, const double *data,
+                      int64_t width, int32_t *idx, double *coef)
+{
+    for (int b = 0; b < nrows; ++b) {
+        int64_t k = 0;
+        for (int64_t e = indptr[b]; e < indptr[b + 1]; ++e, ++k) {
+            idx[(int64_t)b * width + k] = indices[e];
+            coef[(int64_t)b * width + k] = data[e];
+        }
+        for (; k < width; ++k) {
+            idx[(int64_t)b * width + k] = -1;
+            coef[(int64_t)b * width + k] = 0.0;
+        }
+    }
+}
+
+/*
+ * The forward (the sums of orc_integrate) through the look-up table: each bin's slots in
+ * order; a padding pair contributes nothing.
+ */
+void orc_integrate_lut(int nrows, int64_t width, const int32_t *idx, const double *coef,
+                       const double *img, const double *dark, const double *flat, const double *sa,
+                       const double *pol, double *I, double *S, double *N, double *C)
+{
+    for (int b = 0; b < nrows; ++b) {
+        double s = 0.0, n = 0.0, c = 0.0;
+        for (int64_t k = 0; k < width; ++k) {
+            int32_t p = idx[(int64_t)b * width + k];
+            if (p < 0) continue;
+            double w = coef[(int64_t)b * width + k];
+            double v = img[p] - (dark ? dark[p] : 0.0);
+            double nrm = (flat ? flat[p] : 1.0) * (sa ? sa[p] : 1.0) * (pol ? pol[p] : 1.0);
+            s += w * v;
+            n += w * nrm;
+            c += w;
+        }
+        S[b] = s;
+        N[b] = n;
+        C[b] = c;
+        I[b] = (n != 0.0) ? s / n : 0.0;
+    }
+}
