@@ -182,9 +182,11 @@ def ncu_traffic():
     return float(t.group(1))
 
 
-def cpu_baseline(w, seconds, rank=0):
+def cpu_baseline(w, seconds, check=None):
     """The oracle, as it stands, on a bounded sample of the workload: frames integrated one
-    after the other on one host core for about `seconds` (matrix built beforehand, untimed)."""
+    after the other on one host core for about `seconds` (matrix built beforehand, untimed).
+    With check = (frame, I_gpu, solid_angle, polarisation) the oracle's matrix also gives the
+    parity spot check of the GPU's I of that frame (its relative error, and both nnz)."""
     import oracle as O
     from paper_1412_6367_gb300 import synth
     og = O.Geometry(*w.geometry.astuple())
@@ -204,9 +206,16 @@ def cpu_baseline(w, seconds, rank=0):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
+    parity = None
+    if check is not None:
+        frame, got, sa_g, pol_g = check
+        ref = O.integrate(A, frame, dark, flat, sa_g, pol_g)[0]
+        sel = np.abs(ref) > 1e-3 * np.abs(ref).max()
+        parity = {"max_rel_err_I": float(np.max(np.abs(got[sel] - ref[sel]) / np.abs(ref[sel]))),
+                  "nnz_oracle": int(A.nnz)}
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d Pilatus-6M frames integrated one by one by the C oracle (FP64, full "
-                      "split, corrections) in %.1f s; matrix built beforehand" % (n, el)}, A
+                      "split, corrections) in %.1f s; matrix built beforehand" % (n, el)}, parity
 
 
 def run_reference(args):
@@ -262,6 +271,56 @@ def _event_ms(torch, fn, reps):
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
+
+
+def stage_breakdown(torch, dev, reps=20):
+    """Per-stage times of one Pilatus-1M int32 frame (1043 x 981, 1000 q bins, bounding-box
+    split, corrections) integrated one frame per call from a pinned host buffer, the steps of
+    the paper's table in Sec. 6.4: host-to-device copy of the image, the kernels by kind (the
+    cast is fused into them), device-to-host copies of I, S and C, and the Python-level total
+    of copy + integrate + copies back (wall clock, synchronised), for the tiled and the
+    look-up-table layouts."""
+    from paper_1412_6367_gb300 import api, synth
+    w = synth.pilatus1m_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "bbox", mask=mask, device=dev)
+    crad, _ = g.positions(w.ny, w.nx, "q_nm^-1", "centres", chi=False, device=dev)
+    img_h = torch.from_numpy(synth.ring_image(crad.cpu().numpy(), seed=5).view(np.int32)).pin_memory()
+    dark, flat = (torch.from_numpy(a).to(dev) for a in synth.dark_flat(w.ny, w.nx, w.seed))
+    sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
+    img_d = torch.empty_like(img_h, device=dev)
+    outs = [torch.empty(ig.nrows, device=dev) for _ in range(3)]
+    hosts = [torch.empty(ig.nrows).pin_memory() for _ in range(3)]
+    res = {"workload": w.name, "nnz": ig.info["nnz"]}
+    for layout in ("tiled", "lut"):
+        ig.set_layout(layout)
+        call = lambda: ig.integrate(img_d, dark, flat, sa, pol, precision="fp32")
+        img_d.copy_(img_h, non_blocking=True)
+        call()
+        torch.cuda.synchronize()
+        h2d = _event_ms(torch, lambda: img_d.copy_(img_h, non_blocking=True), reps)
+        r = call()
+        d2h = _event_ms(torch, lambda: [hh.copy_(t, non_blocking=True) for hh, t in
+                                        zip(hosts, (r.I, r.sum_signal, r.count))], reps)
+        ig.profile_read()
+        ig.profile_enable(True)
+        for _ in range(reps):
+            call()
+        ig.profile_enable(False)
+        kinds = {k: v[1] / reps for k, v in ig.profile_read().items() if v[0]}
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            img_d.copy_(img_h, non_blocking=True)
+            r = call()
+            for hh, t in zip(hosts, (r.I, r.sum_signal, r.count)):
+                hh.copy_(t, non_blocking=True)
+            torch.cuda.synchronize()
+        total = (time.perf_counter() - t0) / reps * 1e3
+        res[layout] = {"python_total_ms": total, "h2d_image_ms": h2d, "d2h_3_outputs_ms": d2h,
+                       "kernels_ms": kinds, "device_sum_ms": h2d + d2h + sum(kinds.values())}
+    ig.set_layout("tiled")
+    return res
 
 
 def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
@@ -323,6 +382,19 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
         ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32")
     ms = _event_ms(torch, lambda: ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32"), 20)
     out["pilatus_single_frame_fp32"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
+
+    # the same frame through the look-up-table layout (Sec. 5.2), FP32 and FP64
+    lut = {}
+    for prec in ("fp32", "fp64"):
+        ig_pilatus.integrate_lut(img, dark, flat, sa, pol, precision=prec)
+        lut[prec + "_ms_per_frame"] = _event_ms(
+            torch, lambda: ig_pilatus.integrate_lut(img, dark, flat, sa, pol, precision=prec), 10)
+    info = ig_pilatus.refresh_info()
+    lut["width"] = info["lut_width"]
+    lut["slots_per_entry"] = info["lut_width"] * info["nrows"] / info["nnz"]
+    lut["tiled_fp32_ms_per_frame"] = out["pilatus_single_frame_fp32"]["ms_per_frame"]
+    out["pilatus_single_frame_lut"] = lut
+    out["pilatus1m_stages"] = stage_breakdown(torch, dev)
 
     # propagated Poisson variance of the bin sums, 64 Pilatus frames per call
     fr64 = img.view(torch.int32).unsqueeze(0).expand(64, -1, -1).contiguous().view(torch.uint32)
@@ -400,18 +472,8 @@ def main():
         step()
     torch.cuda.synchronize()
 
-    # parity spot check at full size against the oracle (the first frame)
-    parity = None
-    if rank == 0:
-        import oracle as O
-        og = O.Geometry(*w.geometry.astuple())
-        rad, chi = O.corner_positions(og, w.ny, w.nx, w.unit)
-        A = O.csr_build(w.ny, w.nx, rad, chi, mask, w.npt_rad, 0, w.split)
-        ref = O.integrate(A, base[0], dark, flat, sa_d.cpu().numpy(), pol_d.cpu().numpy())
-        got = out.I[0].cpu().numpy().astype(np.float64)
-        sel = np.abs(ref[0]) > 1e-3 * np.abs(ref[0]).max()
-        parity = {"max_rel_err_I": float(np.max(np.abs(got[sel] - ref[0][sel]) / np.abs(ref[0][sel]))),
-                  "nnz_oracle": int(A.nnz), "nnz_gpu": int(info["nnz"])}
+    # the first frame's I, for the parity spot check of the CPU-baseline leg
+    I0 = out.I[0].cpu().numpy().astype(np.float64)
 
     # timed region (device-resident inputs)
     clocks = Clocks(local)
@@ -494,9 +556,11 @@ def main():
         torch.cuda.empty_cache()
         others = other_workloads(torch, dev, ig, (fb0, dark_d, flat_d, sa_d, pol_d))
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_baseline(w, args.cpu_seconds)
+        cpu, parity = cpu_baseline(w, args.cpu_seconds,
+                                   check=(base[0], I0, sa_d.cpu().numpy(), pol_d.cpu().numpy()))
+        parity["nnz_gpu"] = int(info["nnz"])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -79,6 +79,8 @@ typedef struct {
     int64_t device_bytes;      /* device memory owned by the integrator */
     int32_t copy_engine;       /* AZ_COPY_TMA or AZ_COPY_ASYNC */
     int32_t n_items;           /* work items of the forward: tiles, heavy ones cut in several */
+    int32_t layout;            /* AZ_LAYOUT_TILED or AZ_LAYOUT_LUT: what az_integrate1d/2d use */
+    int64_t lut_width;         /* slots per row of the look-up table (0 until it is built) */
 } az_info;
 
 /* ---- geometry (Sec. 3) ---------------------------------------------------------------- */
@@ -326,7 +328,11 @@ void az_multi_destroy(az_multi *plan);
  * Pick the pixel tile shape, rows per warp and frames per pass for this integrator by
  * timing the batched forward on n_trial_frames synthetic frames (allocated and freed
  * inside), then keep the fastest.  Rebuilds the tiled layout if the tile shape changes.
- * Synchronises `stream`.  *best_ms (may be NULL) receives the best time per frame.
+ * Then times one FP32 frame through the tiled form and through the look-up table (built for
+ * the trial if missing, unless it would take more than four times the memory of the CSR
+ * matrix's entries) and sets the single-frame layout (az_set_layout) to the faster; a table
+ * built only for the trial is freed again if it loses.  Synchronises `stream`.  *best_ms
+ * (may be NULL) receives the best time per frame of the batched forward.
  */
 int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t stream, double *best_ms);
 
@@ -336,13 +342,61 @@ int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t stream, double
 int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_per_warp,
                   int frames_per_pass);
 
+/* ---- look-up-table layout (Sec. 5.2) ------------------------------------------------------ */
+
+/*
+ * The matrix as a look-up table (Sec. 5.2, "scatter to gather"): for every output row the
+ * (pixel index, coefficient) pairs it gathers from, in column order, padded with pairs
+ * (-1, 0) to the length of the longest row, the table's width.  It is the paper's
+ * array-of-structures alternative to the CSR form (Sec. 5.2.1, 6.1, 6.3), kept here as a
+ * candidate layout of the single-frame forward.  Device storage is slot-major ([width][nrows]
+ * pairs, so that the threads of a warp, which take consecutive rows, read consecutive pairs):
+ * 8-byte pairs {int32 pixel, float coefficient} for AZ_PREC_FP32_COMP, 16-byte pairs
+ * {int32 pixel, int32 0, double coefficient} for AZ_PREC_FP64, plus a per-pixel buffer of the
+ * corrected frame and the per-chunk partial sums.  Owned by the integrator, freed with it.
+ */
+#define AZ_LAYOUT_TILED 0 /* the tiled CSR form (default) */
+#define AZ_LAYOUT_LUT 1   /* the look-up table */
+
+/* Build (or rebuild) the table of `precision` from the integrator's matrix on `stream`;
+ * synchronises `stream` (the width is read back).  AZ_ENOMEM if it does not fit. */
+int az_lut_build(az_integrator *h, int precision, az_stream_t stream);
+
+/* The table as built.  *width (may be NULL) receives the slots per row (0 if no table was
+ * built).  The host arrays, each NULL or [nrows][width] row-major with the padding:
+ * pixel_host the pixel indices, coef32_host / coef64_host the coefficients of the FP32 /
+ * FP64 table.  AZ_EINVAL if an array is asked of a table that is not built. Synchronous. */
+int az_lut_export(const az_integrator *h, int64_t *width, int32_t *pixel_host, float *coef32_host,
+                  double *coef64_host);
+
+/*
+ * One frame through the table: the four outputs of az_integrate1d / az_integrate2d (same
+ * arguments, shapes, output types and error codes).  Three launches: a correction pass over
+ * the pixels (cast, dark subtracted, flat * solid angle * polarisation formed: the separate
+ * correction step of Sec. 6.4), the gather over each row's pairs, every row cut into chunks
+ * summed by separate threads, and a pass that combines each row's chunk sums in a fixed order
+ * (FP32: compensated) and forms I = S / N (0 where N = 0).  Deterministic.  Builds the table
+ * of `precision` first if it is missing (allocates, synchronises `stream`).
+ */
+int az_integrate_lut(az_integrator *h, const void *image_dev, int image_dtype, const float *dark,
+                     const float *flat, const float *solid_angle, const float *polarization,
+                     int precision, void *out_I, void *out_sum_signal, void *out_sum_norm,
+                     void *out_count, az_stream_t stream);
+
+/* Which layout az_integrate1d / az_integrate2d use: AZ_LAYOUT_TILED or AZ_LAYOUT_LUT (the
+ * table of the call's precision is built on the first call that needs it).  The batched,
+ * variance, adjoint and many-instance entry points always use the tiled form.  az_autotune
+ * sets it to whichever layout integrates one frame faster.  AZ_EINVAL for another value. */
+int az_set_layout(az_integrator *h, int layout);
+
 /* ---- kernel timing --------------------------------------------------------------------- */
 
 /* Per-kernel totals recorded while profiling is enabled.  Kinds: 0 = phase-1 frames kernel
  * (az_integrate_batch*), 1 = phase-1 kernel of the frame-independent sums N and C,
- * 2 = phase-1 single-frame kernel (az_integrate1d/2d), 3 = phase-2 (finalise) kernel,
+ * 2 = phase-1 single-frame kernel (az_integrate1d/2d; with the look-up table, its gather),
+ * 3 = phase-2 (finalise) kernel (with the look-up table, the chunk combination),
  * 4 = per-call preparation (per-entry dark gather, per-pixel flat * solid angle *
- * polarisation) of az_integrate_batch*. */
+ * polarisation of az_integrate_batch*; the look-up table's correction pass). */
 #define AZ_PROF_KINDS 5
 typedef struct {
     int64_t launches[AZ_PROF_KINDS];

@@ -37,7 +37,8 @@ class Info(ctypes.Structure):
                 ("rows_per_warp", ctypes.c_int32), ("frames_per_pass", ctypes.c_int32),
                 ("n_tiles", ctypes.c_int64), ("n_segments", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("copy_engine", ctypes.c_int32),
-                ("n_items", ctypes.c_int32)]
+                ("n_items", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("lut_width", ctypes.c_int64)]
 
 
 class Profile(ctypes.Structure):
@@ -81,6 +82,10 @@ SIGNATURES = {
     "az_multi_destroy": ([vp], None),
     "az_autotune": ([vp, i32, vp, ctypes.POINTER(ctypes.c_double)], i32),
     "az_set_tuning": ([vp, i32, i32, i32, i32], i32),
+    "az_lut_build": ([vp, i32, vp], i32),
+    "az_lut_export": ([vp, vp, vp, vp, vp], i32),
+    "az_integrate_lut": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
+    "az_set_layout": ([vp, i32], i32),
     "az_profile_enable": ([vp, i32], i32),
     "az_set_copy_engine": ([vp, i32], i32),
     "az_profile_read": ([vp, ctypes.POINTER(Profile)], i32),

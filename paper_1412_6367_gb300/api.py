@@ -371,6 +371,53 @@ class Integrator:
         check(self._lib.az_set_tuning(self._h, tile_h, tile_w, rows_per_warp, frames_per_pass))
         self.refresh_info()
 
+    # ---- look-up-table layout (Sec. 5.2) ----
+    def lut_build(self, precision="fp32"):
+        """Build the look-up table of `precision` (az_lut_build); returns its width."""
+        check(self._lib.az_lut_build(self._h, _code(PRECISIONS, precision, "precision"),
+                                     _stream(self.device)))
+        self.refresh_info()
+        return self.info["lut_width"]
+
+    def lut_export(self, precision="fp32"):
+        """(pixel int32, coefficient) numpy arrays [nrows][width] of the table built for
+        `precision` (float32 or float64 coefficients), padding (-1, 0) included."""
+        width = ctypes.c_int64(0)
+        check(self._lib.az_lut_export(self._h, ctypes.byref(width), None, None, None))
+        shape = (self.nrows, width.value)
+        pix = np.empty(shape, np.int32)
+        fp64 = _code(PRECISIONS, precision, "precision") == L.PREC_FP64
+        coef = np.empty(shape, np.float64 if fp64 else np.float32)
+        c = ctypes.c_void_p(coef.ctypes.data)
+        check(self._lib.az_lut_export(self._h, None, ctypes.c_void_p(pix.ctypes.data),
+                                      None if fp64 else c, c if fp64 else None))
+        return pix, coef
+
+    def integrate_lut(self, image, dark=None, flat=None, solid_angle=None, polarization=None,
+                      precision="fp32", out=None) -> Result:
+        """One frame through the look-up table (az_integrate_lut); returns (I, S, N, C)
+        shaped as integrate() returns them."""
+        prec = _code(PRECISIONS, precision, "precision")
+        npix = self.info["ny"] * self.info["nx"]
+        img = _dev(image, "image", numel=npix)
+        dt = torch.float64 if prec == L.PREC_FP64 else torch.float32
+        if out is None:
+            out = Result(*(torch.empty(self.nrows, dtype=dt, device=image.device) for _ in range(4)))
+        check(self._lib.az_integrate_lut(
+            self._h, img, image_dtype_code(image), *self._corr(dark, flat, solid_angle, polarization),
+            prec, _dev(out.I, "I", dt), _dev(out.sum_signal, "S", dt),
+            _dev(out.sum_norm, "N", dt), _dev(out.count, "C", dt), _stream(image.device)))
+        if self.info["npt_azim"]:
+            shp = (self.info["npt_azim"], self.info["npt_rad"])
+            out = Result(*(t.view(shp) for t in out))
+        return out
+
+    def set_layout(self, layout):
+        """The single-frame layout of integrate(): "tiled" or "lut" (az_set_layout)."""
+        code = {"tiled": 0, "lut": 1}[layout] if isinstance(layout, str) else int(layout)
+        check(self._lib.az_set_layout(self._h, code))
+        self.refresh_info()
+
 
 class MultiPlan:
     """Several integrators of uneven shape in one persistent launch (az_multi_create)."""

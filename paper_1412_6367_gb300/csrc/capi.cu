@@ -82,6 +82,8 @@ int build_common(int ny, int nx, const double *rad, const double *chi, int npt_r
     return AZ_OK;
 }
 
+}  // namespace
+
 int check_forward(const az_integrator *h, const void *image, int dtype, const float *dark,
                   const float *flat, const float *sa, const float *pol, const char *who) {
     if (!h) return fail(AZ_EINVAL, "%s: NULL integrator", who);
@@ -92,8 +94,6 @@ int check_forward(const az_integrator *h, const void *image, int dtype, const fl
         if (p && !aligned4(p)) return fail(AZ_EINVAL, "%s: arrays must be 4-byte aligned", who);
     return AZ_OK;
 }
-
-}  // namespace
 
 int fail(int code, const char *fmt, ...) {
     va_list ap;
@@ -171,13 +171,16 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
     out->n_tiles = h->tl.ntiles; out->n_segments = h->tl.nseg;
     out->copy_engine = h->copy_engine;
     out->n_items = h->tl.n_active;
+    out->layout = h->layout;
+    out->lut_width = h->lut_width;
     const DevBuf *bufs[] = {&h->csr_ptr, &h->csr_idx, &h->csr_w64, &h->csc_ptr, &h->csc_row,
                             &h->csc_w64, &h->csc_w32, &h->tl.tile_seg_ptr, &h->tl.tile_ent_ptr,
                             &h->tl.active_tiles, &h->tl.seg_ent_ptr, &h->tl.seg_slot,
                             &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_w32, &h->tl.ent_w64,
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
                             &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
-                            &h->tl.norm_frames, &h->tl.ent_wnorm};
+                            &h->tl.norm_frames, &h->tl.ent_wnorm, &h->lut32, &h->lut64,
+                            &h->lut_vals, &h->lut_part};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;
@@ -232,6 +235,8 @@ static int integrate_common(const az_integrator *h, const void *image, int dtype
     if (two_d && h->npt_azim == 0) return fail(AZ_ESHAPE, "%s: integrator is 1D", who);
     if (!two_d && h->npt_azim != 0) return fail(AZ_ESHAPE, "%s: integrator is 2D", who);
     const_cast<az_integrator *>(h)->last_stream = (cudaStream_t)stream;
+    if (h->layout == AZ_LAYOUT_LUT)
+        return lut_forward(h, image, dtype, dark, flat, sa, pol, precision, oI, oS, oN, oC, (cudaStream_t)stream);
     if (precision == AZ_PREC_FP32_COMP) {
         // the batched machinery on a batch of one frame: the same arithmetic per frame as
         // the single-frame kernel (which remains the path without the tensor-copy engine)
@@ -510,6 +515,73 @@ extern "C" int az_set_tuning(az_integrator *h, int tile_h, int tile_w, int rows_
     return AZ_OK;
 }
 
+// One FP32 frame through the tiled form and through the look-up table; the faster becomes
+// the single-frame layout.  The table is built for the trial if missing and small enough
+// (at most four times the bytes of the matrix's entries), and freed again if it loses.
+static int tune_layout(az_integrator *h, const void *frame, const float *dark, cudaStream_t s) {
+    const bool had_table = h->lut32.p != nullptr;
+    if (!had_table) {
+        int64_t wmax = 0;
+        {
+            std::vector<int32_t> ptr((size_t)h->nrows + 1);
+            AZ_CUDA(cudaMemcpy(ptr.data(), h->csr_ptr.p, sizeof(int32_t) * ptr.size(), cudaMemcpyDeviceToHost));
+            for (int b = 0; b < h->nrows; ++b) wmax = std::max<int64_t>(wmax, ptr[b + 1] - ptr[b]);
+        }
+        if (wmax * h->nrows > 4 * std::max<int64_t>(h->nnz, 1)) return AZ_OK;  // the tiled form stays
+        if (lut_build(h, AZ_PREC_FP32_COMP, s) != AZ_OK) {
+            clear_error();
+            return AZ_OK;
+        }
+    }
+    DevBuf out;
+    AZ_TRY(out.alloc(sizeof(float) * 4 * (size_t)h->nrows));
+    float *o = out.as<float>();
+    const int rows = h->nrows;
+    cudaEvent_t e0, e1;
+    AZ_CUDA(cudaEventCreate(&e0));
+    AZ_CUDA(cudaEventCreate(&e1));
+    double t[2] = {1e30, 1e30};
+    for (int lay = 0; lay < 2; ++lay) {
+        h->layout = lay;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, s);
+            int rc;
+            if (lay == AZ_LAYOUT_LUT) {
+                rc = lut_forward(h, frame, AZ_DTYPE_U32, dark, nullptr, nullptr, nullptr, AZ_PREC_FP32_COMP, o,
+                                 o + rows, o + 2 * rows, o + 3 * rows, s);
+            } else {
+                // what az_integrate1d/2d run in FP32 with the tiled form
+                rc = forward_batch_one(h, frame, AZ_DTYPE_U32, dark, nullptr, nullptr, nullptr, o, o + rows,
+                                       o + 2 * rows, o + 3 * rows, s);
+                if (rc == AZ_EUNSUPPORTED)
+                    rc = forward_single(h, frame, AZ_DTYPE_U32, dark, nullptr, nullptr, nullptr, AZ_PREC_FP32_COMP,
+                                        o, o + rows, o + 2 * rows, o + 3 * rows, s);
+            }
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rc != AZ_OK) {
+                clear_error();
+                break;
+            }
+            if (rep > 0) t[lay] = std::min<double>(t[lay], ms);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->layout = t[AZ_LAYOUT_LUT] < t[AZ_LAYOUT_TILED] ? AZ_LAYOUT_LUT : AZ_LAYOUT_TILED;
+    if (h->layout == AZ_LAYOUT_TILED && !had_table) {
+        h->lut32.release();
+        if (!h->lut64.p) {
+            h->lut_vals.release();
+            h->lut_part.release();
+            h->lut_width = 0;
+        }
+    }
+    return AZ_OK;
+}
+
 extern "C" int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t stream,
                            double *best_ms) {
     clear_error();
@@ -571,6 +643,7 @@ extern "C" int az_autotune(az_integrator *h, int n_trial_frames, az_stream_t str
     h->frames_per_pass = bf;
     h->rows_per_warp = 32 / bf;
     h->copy_engine = be;
+    AZ_TRY(tune_layout(h, frames.p, dark.as<float>(), s));
     AZ_CUDA(cudaStreamSynchronize(s));
     if (best_ms) *best_ms = best / n_trial_frames;
     return AZ_OK;

@@ -132,6 +132,24 @@ struct Profiler {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
+
+// Optional CUDA-event bracket around one launch.
+struct ProfScope {
+    Profiler *p;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(Profiler *p_, int kind_, cudaStream_t s_) : p(p_ && p_->on ? p_ : nullptr), kind(kind_), s(s_) {
+        if (p) { a = p->get(); cudaEventRecord(a, s); }
+    }
+    ~ProfScope() {
+        if (p) {
+            cudaEvent_t b = p->get();
+            cudaEventRecord(b, s);
+            p->recs.push_back({kind, a, b});
+        }
+    }
+};
 }  // namespace azint
 
 struct az_integrator {
@@ -154,6 +172,11 @@ struct az_integrator {
     azint::DevBuf norm;        // [2][nrows] (N, C) in the batch accumulation type
     azint::DevBuf adj;         // [2][nrows] doubles: adjoint row factors g/N and g I/N
     azint::DevBuf status;      // int32 device status word
+    // look-up-table layout (built on request): [width][nrows] pairs, per-pixel corrected
+    // (value, normalisation) of the current frame, per-chunk partial sums
+    azint::DevBuf lut32, lut64, lut_vals, lut_part;
+    int64_t lut_width = 0;
+    int layout = AZ_LAYOUT_TILED;  // what az_integrate1d/2d use
     // host copies for the end-to-end path
     azint::DevBuf host_stage;  // device frames buffer for az_integrate_batch_host
     cudaStream_t last_stream = nullptr;
@@ -194,6 +217,14 @@ int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float
 int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
                     const float *flat, const float *sa, const float *pol, float *oI, float *oU,
                     float *oC, cudaStream_t s);
+// argument checks shared by the forward entry points (NULL, dtype, 4-byte alignment)
+int check_forward(const az_integrator *h, const void *image, int dtype, const float *dark,
+                  const float *flat, const float *sa, const float *pol, const char *who);
+int lut_build(az_integrator *h, int precision, cudaStream_t s);
+int lut_forward(const az_integrator *h, const void *img, int dtype, const float *dark, const float *flat,
+                const float *sa, const float *pol, int precision, void *oI, void *oS, void *oN, void *oC,
+                cudaStream_t s);
+int lut_export(const az_integrator *h, int64_t *width, int32_t *pix, float *c32, double *c64);
 int forward_batch_one(az_integrator *h, const void *image, int dtype, const float *dark,
                       const float *flat, const float *sa, const float *pol, float *oI, float *oS,
                       float *oN, float *oC, cudaStream_t s);

@@ -1245,24 +1245,6 @@ Inst make_inst(const az_integrator *h, bool fp64) {
     return d;
 }
 
-// Optional CUDA-event bracket around one launch.
-struct ProfScope {
-    Profiler *p;
-    int kind;
-    cudaStream_t s;
-    cudaEvent_t a = nullptr;
-    ProfScope(Profiler *p_, int kind_, cudaStream_t s_) : p(p_ && p_->on ? p_ : nullptr), kind(kind_), s(s_) {
-        if (p) { a = p->get(); cudaEventRecord(a, s); }
-    }
-    ~ProfScope() {
-        if (p) {
-            cudaEvent_t b = p->get();
-            cudaEventRecord(b, s);
-            p->recs.push_back({kind, a, b});
-        }
-    }
-};
-
 template <class AT, class WT, int MODE, int NIMG, int DT, bool TMA>
 int run_phase1(const Inst &single, const Inst *multi, int n_inst, int64_t n_items,
                const StageGeom &sg, const TmaSet &tm, cudaStream_t s, Profiler *prof = nullptr) {

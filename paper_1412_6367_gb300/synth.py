@@ -74,6 +74,22 @@ def pilatus_workload(seed: int = 1, split: int = SPLIT_FULL, npt: int = 1000) ->
                     image_dtype="uint32", masked=True, corrections=True, seed=seed)
 
 
+def pilatus1m_workload(seed: int = 1, split: int = SPLIT_BBOX, npt: int = 1000) -> Workload:
+    """Pilatus-1M shape of the paper's stage timings (Sec. 6.4: 981 x 1043 signed 32-bit
+    pixels): 1043 rows x 981 columns (5 x 2 modules of 195 x 487 pixels, gaps of 17 rows and
+    7 columns), int32, 172 um, 200 mm, PONI at the centre +- U(-5, 5) mm per axis,
+    rot1 = 0.02, rot2 = 0.01, q in nm^-1, 1000 bins, bounding-box split (the paper's
+    benchmarks split by bounding box, Sec. 6), module-gap mask, corrections."""
+    rng = np.random.default_rng(seed)
+    ny, nx, px = 1043, 981, 172e-6
+    off = rng.uniform(-5e-3, 5e-3, size=2)
+    g = GeometryParams(dist=0.2, poni1=ny * px / 2 + off[0], poni2=nx * px / 2 + off[1],
+                       rot1=0.02, rot2=0.01, rot3=0.0, pixel1=px, pixel2=px,
+                       wavelength=1.0e-10)
+    return Workload("pilatus1m-1043x981-q-bbox-%d" % npt, ny, nx, g, UNIT_Q_NM, split, npt,
+                    image_dtype="int32", masked=True, corrections=True, seed=seed)
+
+
 def cake_workload(seed: int = 2) -> Workload:
     """2048 x 2048 float32, 50 um, 150 mm, rot1 = 0.05, PONI at the detector centre (a pixel
     corner), 500 2theta x 360 chi bins, full split, corrections as the Pilatus case."""

@@ -53,3 +53,15 @@ def test_host_only_calls():
     L = _lib.load()
     assert L.az_integrate1d(None, None, 0, None, None, None, None, 1, None, None, None, None, None) == -1
     assert b"NULL" in L.az_last_error()
+
+
+def test_host_only_lut_calls():
+    """The look-up-table entry points refuse NULL handles (and bad arguments) before touching
+    a device."""
+    from paper_1412_6367_gb300 import _lib
+    L = _lib.load()
+    assert L.az_lut_build(None, 1, None) == -1
+    assert L.az_lut_export(None, None, None, None, None) == -1
+    assert L.az_integrate_lut(None, None, 0, None, None, None, None, 1, None, None, None, None, None) == -1
+    assert L.az_set_layout(None, 1) == -1
+    assert b"az_set_layout" in L.az_last_error()
