@@ -180,7 +180,7 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
                             &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
                             &h->tl.norm_frames, &h->tl.ent_wnorm, &h->lut32, &h->lut64,
-                            &h->lut_vals, &h->lut_part};
+                            &h->lut_vals, &h->lut_part, &h->one_planes};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;

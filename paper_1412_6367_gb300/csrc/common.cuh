@@ -175,6 +175,8 @@ struct az_integrator {
     // look-up-table layout (built on request): [width][nrows] pairs, per-pixel corrected
     // (value, normalisation) of the current frame, per-chunk partial sums
     azint::DevBuf lut32, lut64, lut_vals, lut_part;
+    // single FP32 frame through the frames kernel: [2][ny*nx] corrected frame and normalisation
+    azint::DevBuf one_planes;
     int64_t lut_width = 0;
     int layout = AZ_LAYOUT_TILED;  // what az_integrate1d/2d use
     // host copies for the end-to-end path

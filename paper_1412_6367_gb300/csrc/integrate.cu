@@ -64,6 +64,8 @@ struct Inst {
     const int32_t *tile_desc, *tile_rec;  // per active tile: descriptor [8] and record
     const float *ent_dark;                // frames pass: dark of each entry's pixel (or NULL)
     const CUtensorMap *maps;              // many-instance launch: this instance's [5][4] maps
+    int single_nc;  // single-frame phase 2 in FP32: 0 S, N, C from the partials; 1 C from
+                    // the per-layout cache norm[nrows..]; 2 N and C from that cache (N == C)
 };
 
 struct StageGeom {
@@ -1152,8 +1154,8 @@ __global__ void phase2_kernel(const __grid_constant__ Inst single, const Inst *_
             const AT *P = static_cast<const AT *>(d.partial);
             if (MODE == MODE_SINGLE) {
                 const AT S = row_sum<AT>(P, a, b);
-                const AT N = row_sum<AT>(P + d.nseg, a, b);
-                const AT C = row_sum<AT>(P + 2 * (size_t)d.nseg, a, b);
+                const AT N = d.single_nc == 2 ? (AT)d.norm[d.nrows + r] : row_sum<AT>(P + d.nseg, a, b);
+                const AT C = d.single_nc ? (AT)d.norm[d.nrows + r] : row_sum<AT>(P + 2 * (size_t)d.nseg, a, b);
                 if (lane == 0) {
                     const AT I = N != AT(0) ? S / N : AT(0);
                     if (d.oI) static_cast<AT *>(d.oI)[r] = I;
@@ -1528,6 +1530,29 @@ __global__ void gather_wnorm_kernel(const int32_t *__restrict__ pix, const float
     }
 }
 
+// One frame's two planes for the frames kernel: [cast(img) - dark] and, with corrections,
+// [((1 * flat) * solid angle) * polarisation] -- the values the batched path forms per entry
+// (dark) and in its norm pass, with the same roundings.
+template <int DT>
+__global__ void single_planes_kernel(const void *__restrict__ img, const float *__restrict__ dark,
+                                     const float *__restrict__ flat, const float *__restrict__ sa,
+                                     const float *__restrict__ pol, int64_t n, int with_norm,
+                                     float *__restrict__ out) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        float v = img_f32<DT>(static_cast<const uint32_t *>(img)[p]);
+        if (dark) v = __fsub_rn(v, dark[p]);
+        out[p] = v;
+        if (with_norm) {
+            float m = 1.f;
+            if (flat) m = __fmul_rn(m, flat[p]);
+            if (sa) m = __fmul_rn(m, sa[p]);
+            if (pol) m = __fmul_rn(m, pol[p]);
+            out[n + p] = m;
+        }
+    }
+}
+
 __global__ void fill_f32_kernel(float *__restrict__ out, int64_t n, float v) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x)
@@ -1826,8 +1851,34 @@ int forward_batch_one(az_integrator *h, const void *image, int dtype, const floa
                       float *oN, float *oC, cudaStream_t s) {
     if (engine_for(h) != AZ_COPY_TMA || h->partial_bytes < 2 * sizeof(float) * (size_t)h->tl.nseg)
         return AZ_EUNSUPPORTED;
-    AZ_TRY(batch_norm(h, flat, sa, pol, oN, oC, s));
-    return batch_frames(h, image, 1, dtype, dark, oI, oS, 0, s);
+    // C of the current layout, once
+    if (!h->count_ready) AZ_TRY(batch_norm(h, nullptr, nullptr, nullptr, nullptr, nullptr, s));
+    // Three launches: the frame's planes [img - dark; flat * Omega * P], the frames kernel over
+    // them as a batch of two frames (S and N per segment, the accumulation of every other
+    // frame), and phase 2 with C from the cache.  Without flat, solid angle and polarisation
+    // only the first plane is reduced and N = C.
+    const int64_t npix = (int64_t)h->ny * h->nx;
+    const bool corr = flat || sa || pol;
+    if (h->one_planes.bytes < 2 * sizeof(float) * (size_t)npix)
+        AZ_TRY(h->one_planes.alloc(2 * sizeof(float) * (size_t)npix));
+    float *planes = h->one_planes.as<float>();
+    {
+        ProfScope ps(&h->prof, 4, s);
+        const unsigned g = (unsigned)std::min<int64_t>((npix + 255) / 256, (int64_t)num_sms() * 8);
+        const int wn = corr ? 1 : 0;
+        switch (dtype) {
+            case AZ_DTYPE_F32: single_planes_kernel<AZ_DTYPE_F32><<<g, 256, 0, s>>>(image, dark, flat, sa, pol, npix, wn, planes); break;
+            case AZ_DTYPE_U32: single_planes_kernel<AZ_DTYPE_U32><<<g, 256, 0, s>>>(image, dark, flat, sa, pol, npix, wn, planes); break;
+            default: single_planes_kernel<AZ_DTYPE_I32><<<g, 256, 0, s>>>(image, dark, flat, sa, pol, npix, wn, planes); break;
+        }
+        AZ_CUDA(cudaGetLastError());
+    }
+    const int rc = frames_v3(h, planes, corr ? 2 : 1, AZ_DTYPE_F32, nullptr, 2, s);
+    if (rc != AZ_OK) return rc;
+    Inst d = make_inst(h, false);
+    d.oI = oI; d.oS = oS; d.oN = oN; d.oC = oC;
+    d.single_nc = corr ? 1 : 2;
+    return run_phase2<float, MODE_SINGLE>(d, nullptr, 1, h->nrows, 1, s, &h->prof);
 }
 
 int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
