@@ -370,6 +370,12 @@ template <> struct Acc<float> {
             kahan_merge(k, o);
         }
     }
+    // the partner lane's sum merged in, the lower lane's on the left (its value is right on
+    // the lower lane of each pair; the upper lane ends with the pair in the other order)
+    __device__ void merge_lower_left(int m) {
+        const Kahan o = shfl_xor(k, m);
+        if ((threadIdx.x & m) == 0) kahan_merge(k, o);
+    }
     __device__ float value() const { return kahan_value(k); }
 };
 template <> struct Acc<double> {
@@ -378,6 +384,10 @@ template <> struct Acc<double> {
     __device__ void add(double w, double v) { s = __fma_rn(w, v, s); }
     __device__ void merge(const Acc<double> &o) { s += o.s; }
     __device__ void merge_xor(int m) { s += __shfl_xor_sync(0xffffffffu, s, m); }
+    __device__ void merge_lower_left(int m) {
+        const double o = __shfl_xor_sync(0xffffffffu, s, m);
+        if ((threadIdx.x & m) == 0) s = s + o;
+    }
     __device__ double value() const { return s; }
 };
 
@@ -592,12 +602,85 @@ __device__ void consume_single64(const ConsumerParams &cp, const unsigned char *
     }
 }
 
+// Single-frame mode with four lanes per segment: lane j of a segment keeps accumulator j of
+// each of the three sums (the entries e = j mod 4, in order), forming per entry the values of
+// consume_serial (FP32: x = image - dark, n = ((1 flat) solid angle) polarisation, 1, each
+// Kahan-added with its weight) or of consume_single64 (FP64: the same values, fused
+// multiply-adds); the four lanes are merged by shuffles as ((a0 + a1) + (a2 + a3)), the merge
+// of both.  Same operations on the same values, so the same bits, with a quarter of the
+// chain per lane, every lane busy and eight segments per claim.  Without flat, solid angle
+// and polarisation n = 1 for every entry, so N is C and is not formed twice.
+template <class AT, class WT, int DT, bool SE>
+__device__ void consume_single_split(const ConsumerParams &cp, const unsigned char *stage,
+                                     const StageGeom &sg, int *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 3, sub = lane >> 2;
+    const int *h = reinterpret_cast<const int *>(stage);
+    const int ns = h[0];
+    const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
+    const int oimg = h[16];
+    const bool norm1 = oflat < 0 && osa < 0 && opol < 0;
+    const int *slots = reinterpret_cast<const int *>(stage + kHeaderBytes) + 4;
+    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
+    const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
+    const uint16_t *L;
+    const WT *W;
+    if constexpr (SE) {
+        const unsigned char *eb = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
+        L = reinterpret_cast<const uint16_t *>(eb);
+        W = reinterpret_cast<const WT *>(eb + sg.ent_cap * 2u);
+    } else {
+        L = cp.ent_loc + h[8];
+        W = static_cast<const WT *>(cp.ent_w) + h[8];
+    }
+    AT *out = static_cast<AT *>(cp.partial);
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, 8);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        const int sl = b + sub;
+        const bool live = sl < ns;
+        const int e0 = live ? starts[sl] : 0, e1 = live ? starts[sl + 1] : 0, slot = live ? slots[sl] : 0;
+        Acc<AT> aS, aN, aC;
+        aS.zero(); aN.zero(); aC.zero();
+        for (int e = e0 + j; e < e1; e += 4) {
+            const int loc = L[e];
+            const AT w = (AT)W[e];
+            AT x, n = AT(1);
+            if (sizeof(AT) == 8) {
+                x = (AT)img_f64<DT>(planes[oimg + loc]);
+                if (odark >= 0) x = x - (AT)__uint_as_float(planes[odark + loc]);
+            } else {
+                float v = img_f32<DT>(planes[oimg + loc]);
+                if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc]));
+                x = (AT)v;
+            }
+            if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc]);
+            if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc]);
+            if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc]);
+            aS.add(w, x);
+            if (!norm1) aN.add(w, n);
+            aC.add(w, AT(1));
+        }
+        // lanes 0 and 2 form a0 + a1 and a2 + a3 (lower lane on the left); lane 0 adds them
+        aS.merge_lower_left(1); aC.merge_lower_left(1);
+        aS.merge_lower_left(2); aC.merge_lower_left(2);
+        if (!norm1) { aN.merge_lower_left(1); aN.merge_lower_left(2); }
+        if (live && j == 0) {
+            out[slot] = aS.value();
+            out[(size_t)cp.nseg + slot] = norm1 ? aC.value() : aN.value();
+            out[2 * (size_t)cp.nseg + slot] = aC.value();
+        }
+    }
+}
+
 template <class AT, class WT, int MODE, int NIMG, int DT>
 __device__ __forceinline__ void consume_dispatch(const ConsumerParams &cp, const unsigned char *stage,
                                                  const StageGeom &sg, int *ctr) {
-    if constexpr (MODE == MODE_SINGLE && sizeof(AT) == 8) {
-        if (cp.stage_entries) consume_single64<DT, true>(cp, stage, sg, ctr);
-        else consume_single64<DT, false>(cp, stage, sg, ctr);
+    if constexpr (MODE == MODE_SINGLE) {
+        if (cp.stage_entries) consume_single_split<AT, WT, DT, true>(cp, stage, sg, ctr);
+        else consume_single_split<AT, WT, DT, false>(cp, stage, sg, ctr);
     } else {
         constexpr int Q = MODE == MODE_FRAMES ? NIMG : (MODE == MODE_NORM ? 2 : 4);
         if (cp.stage_entries) consume_serial<Q, AT, WT, MODE, DT, true>(cp, stage, sg, ctr);
@@ -948,6 +1031,64 @@ __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, co
     }
 }
 
+// One or two frames per stage: a warp would take 32 or 16 segments at once and run each
+// segment's whole entry stream on one lane, while a tile has only some tens of segments.  Here
+// four lanes share a (segment, frame): lane j keeps accumulator j (the entries e = j mod 4 of
+// every quad, in order, exactly as one lane of fr_consume steps its accumulator j), and the
+// four are merged by shuffles as ((a0 + a1) + (a2 + a3)), the merge of fr_consume.  Same
+// operations on the same values, so the same bits, with a quarter of the chain per lane and
+// 8 / G segments per claim.
+template <int G, int DT, int VM>
+__device__ __forceinline__ void fr_consume_split(const FrArgs &a, const FrGeom &fg, const unsigned char *eb,
+                                                 const uint32_t *planes, const int *hdr, int *ctr) {
+    static_assert(G == 1 || G == 2, "split consumer is for one or two frames per stage");
+    constexpr int R = 8 / G;
+    const int lane = threadIdx.x & 31;
+    const int j = lane & 3, q = (lane >> 2) % G, sub = lane / (4 * G);
+    const int *rec = reinterpret_cast<const int *>(eb);
+    const int ns = rec[1];
+    const int *slots = rec + 4;
+    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
+    const uint16_t *L = reinterpret_cast<const uint16_t *>(eb + fg.rec_cap);
+    const float *W = reinterpret_cast<const float *>(eb + fg.rec_cap + fg.ent_cap * 2u);
+    const float *D = W + fg.ent_cap;
+    const int nimg = hdr[0], g = hdr[1];
+    const bool active = q < nimg;
+    const uint32_t *P = planes + hdr[2 + (active ? q : 0)];
+    float *out = a.partial + (size_t)(g * G + q) * (size_t)a.nseg;
+    while (true) {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, R);
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (b >= ns) break;
+        const int sl = b + sub;
+        int e0 = 0, e1 = 0, slot = 0;
+        if (sl < ns) {
+            e0 = starts[sl];
+            e1 = starts[sl + 1];
+            slot = slots[sl];
+        }
+        if (!active) e1 = e0;
+        Kahan k{0.f, 0.f};
+        for (int e = e0 + j; e < e1; e += 4) {
+            float v = img_f32<DT>(P[L[e]]);
+            float w = W[e];
+            if (VM == VM_VAR) {
+                v = fmaxf(v, 0.f);
+                w = __fmul_rn(w, w);
+            }
+            if (VM == VM_DARK) v = __fsub_rn(v, D[e]);
+            kahan_add(k, w, v);
+        }
+        // lanes j = 0, 2 take (a0 + a1), (a2 + a3); lane 0 then adds the second to the first
+        Kahan o = shfl_xor(k, 1);
+        kahan_merge(k, o);
+        o = shfl_xor(k, 2);
+        kahan_merge(k, o);
+        if (j == 0 && sl < ns && active) out[slot] = kahan_value(k);
+    }
+}
+
 // Bounded grace wait for copies this CTA issued before giving up (every wait is bounded).
 __device__ __forceinline__ void fr_drain(uint64_t *bar, uint32_t parity) { (void)mbar_wait_bounded(bar, parity); }
 
@@ -1036,8 +1177,11 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
                     stop = true;
                     break;
                 }
-                fr_consume<G, DT, VM>(a, fg, ebp, reinterpret_cast<const uint32_t *>(pst + (size_t)s * fg.pstage_bytes),
-                                      hdrs + s * (kFrStageHeader / 4), &ctr[s]);
+                const uint32_t *pl = reinterpret_cast<const uint32_t *>(pst + (size_t)s * fg.pstage_bytes);
+                if constexpr (G <= 2)
+                    fr_consume_split<G, DT, VM>(a, fg, ebp, pl, hdrs + s * (kFrStageHeader / 4), &ctr[s]);
+                else
+                    fr_consume<G, DT, VM>(a, fg, ebp, pl, hdrs + s * (kFrStageHeader / 4), &ctr[s]);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&pempty[s]);
             }
