@@ -165,16 +165,38 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+FRAMES_SECTIONS = (("// frames pass with tile-resident entries", "// phase 2: per-row sums"),
+                   ("// ---- frames kernel with tile-resident entries", "// flat * solid angle * polarisation per pixel"))
+
+
+def frames_kernel_sha():
+    """sha256 of the frames kernel's source: its device and launch sections of integrate.cu
+    and the shared header (None if a section marker is missing)."""
+    csrc = os.path.join(ROOT, "paper_1412_6367_gb300", "csrc")
+    try:
+        text = open(os.path.join(csrc, "integrate.cu")).read()
+        common = open(os.path.join(csrc, "common.cuh")).read()
+    except OSError:
+        return None
+    parts = []
+    for a, b in FRAMES_SECTIONS:
+        i, j = text.find(a), text.find(b)
+        if i < 0 or j < i:
+            return None
+        parts.append(text[i:j])
+    parts.append(common)
+    return hashlib.sha256("".join(parts).encode()).hexdigest()
+
+
 def ncu_traffic():
     """DRAM bytes per launch of the phase-1 frames kernel from the committed ncu summary,
     if that summary was taken on the current source of the kernel."""
     path = os.path.join(ROOT, "profiles", "frames_kernel_pilatus6m.txt")
-    src = os.path.join(ROOT, "paper_1412_6367_gb300", "csrc", "integrate.cu")
     try:
         text = open(path).read()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
+    sha = frames_kernel_sha()
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", text)
     if not m or not t or m.group(1) != sha:
@@ -360,8 +382,14 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
         plan.launch(use_graph=True)
     ms = _event_ms(torch, lambda: plan.launch(use_graph=True), 10)
     pix = sum(wi.ny * wi.nx for wi in ws)
+    nnz = sum(gi.info["nnz"] for gi in igs)
+    rows = sum(gi.nrows for gi in igs)
+    # algorithmic bytes of the launch: every entry (2-byte location, 4-byte weight), every
+    # image pixel, four outputs per row
+    ab = 6 * nnz + 4 * pix + 16 * rows
     out["batching_64_instances"] = {"ms_per_launch": ms, "instances_per_s": 64 / (ms / 1e3),
-                                    "gpix_per_s": pix / (ms / 1e3) / 1e9}
+                                    "gpix_per_s": pix / (ms / 1e3) / 1e9, "nnz_total": nnz,
+                                    "algorithmic_gbs": ab / (ms / 1e3) / 1e9}
     del plan, igs, imgs
 
     # 4096 frames of 2167 x 2070 uint32 through one matrix (2000 q bins): a 256-frame device

@@ -423,8 +423,7 @@ template <> struct W4<double> {
 // claim counter; the Q lanes of a segment share its entry stream (broadcast reads) and each
 // sums one quantity over all of the segment's entries:
 //   frames pass: quantity q = frame q of the item, value = cast(image) - dark;
-//   norm pass:   q = 0: flat * solid angle * polarisation, q = 1: 1 (the count);
-//   single pass: q = 0: cast(image) - dark, q = 1: the normalisation, q = 2: 1, q = 3 idle.
+//   norm pass:   q = 0: flat * solid angle * polarisation, q = 1: 1 (the count).
 // Segments start on a multiple of 4 entries and hold whole quads (the layout pads them with
 // entries of weight 0 that read the plane's zero band).  Entries are read four at a time (one
 // 8-byte read of the locations, 16-byte reads of the weights and per-entry darks); entry e
@@ -434,6 +433,7 @@ template <> struct W4<double> {
 template <int Q, class AT, class WT, int MODE, int DT, bool SE>
 __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *stage,
                                const StageGeom &sg, int *ctr) {
+    static_assert(MODE != MODE_SINGLE, "the single pass has its own consumer");
     constexpr int R = 32 / Q;
     const int lane = threadIdx.x & 31;
     const int sub = lane / Q, q = lane % Q;
@@ -441,10 +441,7 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
     const int ns = h[0], group = h[1], nimg = h[2];
     const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
     const int oimg = h[16 + (MODE == MODE_FRAMES ? q : 0)];
-    bool active;
-    if (MODE == MODE_FRAMES) active = q < nimg;
-    else if (MODE == MODE_NORM) active = true;
-    else active = q < 3;
+    const bool active = MODE == MODE_FRAMES ? q < nimg : true;
     const int *slots = reinterpret_cast<const int *>(stage + kHeaderBytes) + 4;
     const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
     const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
@@ -500,7 +497,7 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
                     float v = img_f32<DT>(planes[oimg + loc[j]]);
                     if (has_dk) v = __fsub_rn(v, dk[j]);
                     x = (AT)v;
-                } else if (MODE == MODE_NORM) {
+                } else {
                     AT n = AT(1);
                     if (q == 0) {
                         if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc[j]]);
@@ -508,25 +505,6 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
                         if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc[j]]);
                     }
                     x = n;
-                } else {
-                    if (q == 0) {
-                        if (sizeof(AT) == 8) {
-                            x = (AT)img_f64<DT>(planes[oimg + loc[j]]);
-                            if (odark >= 0) x = x - (AT)__uint_as_float(planes[odark + loc[j]]);
-                        } else {
-                            float v = img_f32<DT>(planes[oimg + loc[j]]);
-                            if (odark >= 0) v = __fsub_rn(v, __uint_as_float(planes[odark + loc[j]]));
-                            x = (AT)v;
-                        }
-                    } else if (q == 1) {
-                        AT n = AT(1);
-                        if (oflat >= 0) n = n * (AT)__uint_as_float(planes[oflat + loc[j]]);
-                        if (osa >= 0) n = n * (AT)__uint_as_float(planes[osa + loc[j]]);
-                        if (opol >= 0) n = n * (AT)__uint_as_float(planes[opol + loc[j]]);
-                        x = n;
-                    } else {
-                        x = AT(1);
-                    }
                 }
                 acc[j].add((AT)w[j], x);
             }
@@ -538,78 +516,14 @@ __device__ void consume_serial(const ConsumerParams &cp, const unsigned char *st
     }
 }
 
-// FP64 single-frame reduction with one lane per segment forming all three sums.  The FP64
-// pipe of this GPU is narrow, and the one-lane-per-quantity form of consume_serial leaves
-// three of four lanes idle in every FP64 instruction; here every lane works.  Per sum the
-// operations are those of consume_serial in single mode: x = image - dark,
-// n = ((1 flat) solid angle) polarisation, 1, each multiplied by the weight into accumulator
-// e mod 4, merged as ((a0 + a1) + (a2 + a3)).
-template <int DT, bool SE>
-__device__ void consume_single64(const ConsumerParams &cp, const unsigned char *stage,
-                                 const StageGeom &sg, int *ctr) {
-    const int lane = threadIdx.x & 31;
-    const int *h = reinterpret_cast<const int *>(stage);
-    const int ns = h[0];
-    const int odark = h[3], oflat = h[4], osa = h[5], opol = h[6];
-    const int oimg = h[16];
-    const int *slots = reinterpret_cast<const int *>(stage + kHeaderBytes) + 4;
-    const uint16_t *starts = reinterpret_cast<const uint16_t *>(slots + ns);
-    const uint32_t *planes = reinterpret_cast<const uint32_t *>(stage + kHeaderBytes + sg.rec_cap);
-    const uint16_t *L;
-    const double *W;
-    if constexpr (SE) {
-        const unsigned char *eb = stage + kHeaderBytes + sg.rec_cap + sg.plane_region;
-        L = reinterpret_cast<const uint16_t *>(eb);
-        W = reinterpret_cast<const double *>(eb + sg.ent_cap * 2u);
-    } else {
-        L = cp.ent_loc + h[8];
-        W = static_cast<const double *>(cp.ent_w) + h[8];
-    }
-    double *out = static_cast<double *>(cp.partial);
-    while (true) {
-        int b = 0;
-        if (lane == 0) b = atomicAdd(ctr, 32);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (b >= ns) break;
-        const int sl = b + lane;
-        const bool live = sl < ns;
-        const int e0 = live ? starts[sl] : 0, e1 = live ? starts[sl + 1] : 0, slot = live ? slots[sl] : 0;
-        double aS[4] = {0.0, 0.0, 0.0, 0.0}, aN[4] = {0.0, 0.0, 0.0, 0.0}, aC[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int qd = e0; qd < e1; qd += 4) {
-            const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
-            const int loc[4] = {(int)(l2.x & 0xffffu), (int)(l2.x >> 16), (int)(l2.y & 0xffffu),
-                                (int)(l2.y >> 16)};
-            double w[4];
-            W4<double>::load(W + qd, w);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                double x = img_f64<DT>(planes[oimg + loc[j]]);
-                if (odark >= 0) x = x - (double)__uint_as_float(planes[odark + loc[j]]);
-                double n = 1.0;
-                if (oflat >= 0) n = n * (double)__uint_as_float(planes[oflat + loc[j]]);
-                if (osa >= 0) n = n * (double)__uint_as_float(planes[osa + loc[j]]);
-                if (opol >= 0) n = n * (double)__uint_as_float(planes[opol + loc[j]]);
-                aS[j] = __fma_rn(w[j], x, aS[j]);
-                aN[j] = __fma_rn(w[j], n, aN[j]);
-                aC[j] = __fma_rn(w[j], 1.0, aC[j]);
-            }
-        }
-        if (live) {
-            out[slot] = (aS[0] + aS[1]) + (aS[2] + aS[3]);
-            out[(size_t)cp.nseg + slot] = (aN[0] + aN[1]) + (aN[2] + aN[3]);
-            out[2 * (size_t)cp.nseg + slot] = (aC[0] + aC[1]) + (aC[2] + aC[3]);
-        }
-    }
-}
-
-// Single-frame mode with four lanes per segment: lane j of a segment keeps accumulator j of
-// each of the three sums (the entries e = j mod 4, in order), forming per entry the values of
-// consume_serial (FP32: x = image - dark, n = ((1 flat) solid angle) polarisation, 1, each
-// Kahan-added with its weight) or of consume_single64 (FP64: the same values, fused
-// multiply-adds); the four lanes are merged by shuffles as ((a0 + a1) + (a2 + a3)), the merge
-// of both.  Same operations on the same values, so the same bits, with a quarter of the
-// chain per lane, every lane busy and eight segments per claim.  Without flat, solid angle
-// and polarisation n = 1 for every entry, so N is C and is not formed twice.
+// Single-frame mode, four lanes per segment: lane j of a segment keeps accumulator j of each
+// of the three sums (the entries e = j mod 4, in order), with per entry x = image - dark,
+// n = ((1 flat) solid angle) polarisation and 1, each added with its weight (FP32:
+// compensated; FP64: fused multiply-adds); the four lanes are merged by shuffles as
+// ((a0 + a1) + (a2 + a3)), the order every other reduction of the library uses, so a frame's
+// FP32 sums have the bits of the frames kernel's.  A quarter of the chain per lane, every
+// lane busy, eight segments per claim.  Without flat, solid angle and polarisation n = 1 for
+// every entry, so N is C and is not formed twice.
 template <class AT, class WT, int DT, bool SE>
 __device__ void consume_single_split(const ConsumerParams &cp, const unsigned char *stage,
                                      const StageGeom &sg, int *ctr) {
@@ -682,7 +596,7 @@ __device__ __forceinline__ void consume_dispatch(const ConsumerParams &cp, const
         if (cp.stage_entries) consume_single_split<AT, WT, DT, true>(cp, stage, sg, ctr);
         else consume_single_split<AT, WT, DT, false>(cp, stage, sg, ctr);
     } else {
-        constexpr int Q = MODE == MODE_FRAMES ? NIMG : (MODE == MODE_NORM ? 2 : 4);
+        constexpr int Q = MODE == MODE_FRAMES ? NIMG : 2;
         if (cp.stage_entries) consume_serial<Q, AT, WT, MODE, DT, true>(cp, stage, sg, ctr);
         else consume_serial<Q, AT, WT, MODE, DT, false>(cp, stage, sg, ctr);
     }
