@@ -49,6 +49,11 @@ def parse(argv=None):
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the cake / batching / stream / adjoint measurements")
+    ap.add_argument("--only-batching", action="store_true",
+                    help="run only the many-instance launch (3 warm-up + --steps launches) "
+                         "and print its figures")
+    ap.add_argument("--instances", type=int, default=64,
+                    help="instances of the many-instance launch with --only-batching")
     return ap.parse_args(argv)
 
 
@@ -345,6 +350,33 @@ def stage_breakdown(torch, dev, reps=20):
     return res
 
 
+def batching_workload(torch, dev, gen, reps=10, n=64):
+    """n (default 64) heterogeneous instances (three detector shapes, 500 / 2000 / 5000 q
+    bins, full split) in one graph-captured persistent launch: ms per launch and throughput."""
+    from paper_1412_6367_gb300 import api, synth
+    ws = synth.batch_instances()[:n]
+    igs, imgs = [], []
+    for wi in ws:
+        gi = api.Geometry(*wi.geometry.astuple())
+        igs.append(api.Integrator.build(gi, (wi.ny, wi.nx), wi.npt_rad, 0, "q_nm^-1", "full", device=dev))
+        imgs.append(torch.randint(0, 4000, (wi.ny, wi.nx), generator=gen, device=dev, dtype=torch.int32))
+    plan = api.MultiPlan(igs, imgs)
+    for _ in range(3):
+        plan.launch(use_graph=True)
+    ms = _event_ms(torch, lambda: plan.launch(use_graph=True), reps)
+    pix = sum(wi.ny * wi.nx for wi in ws)
+    nnz = sum(gi.info["nnz"] for gi in igs)
+    rows = sum(gi.nrows for gi in igs)
+    # algorithmic bytes of the launch: every entry (2-byte location, 4-byte weight), every
+    # image pixel, four outputs per row
+    ab = 6 * nnz + 4 * pix + 16 * rows
+    res = {"ms_per_launch": ms, "instances": len(ws), "instances_per_s": len(ws) / (ms / 1e3),
+           "gpix_per_s": pix / (ms / 1e3) / 1e9, "nnz_total": nnz,
+           "algorithmic_gbs": ab / (ms / 1e3) / 1e9}
+    del plan, igs, imgs
+    return res
+
+
 def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     """The other workloads' throughput (device-resident inputs, warm), reported beside the
     headline: the 2D cake, the 64-instance persistent launch, a 4096-frame stream through
@@ -370,27 +402,7 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
                                       "single_frame_fp32_ms": ms1, "nnz": ig.info["nnz"]}
     del frames, ig
 
-    # 64 heterogeneous instances in one graph-captured persistent launch
-    ws = synth.batch_instances()
-    igs, imgs = [], []
-    for wi in ws:
-        gi = api.Geometry(*wi.geometry.astuple())
-        igs.append(api.Integrator.build(gi, (wi.ny, wi.nx), wi.npt_rad, 0, "q_nm^-1", "full", device=dev))
-        imgs.append(torch.randint(0, 4000, (wi.ny, wi.nx), generator=gen, device=dev, dtype=torch.int32))
-    plan = api.MultiPlan(igs, imgs)
-    for _ in range(3):
-        plan.launch(use_graph=True)
-    ms = _event_ms(torch, lambda: plan.launch(use_graph=True), 10)
-    pix = sum(wi.ny * wi.nx for wi in ws)
-    nnz = sum(gi.info["nnz"] for gi in igs)
-    rows = sum(gi.nrows for gi in igs)
-    # algorithmic bytes of the launch: every entry (2-byte location, 4-byte weight), every
-    # image pixel, four outputs per row
-    ab = 6 * nnz + 4 * pix + 16 * rows
-    out["batching_64_instances"] = {"ms_per_launch": ms, "instances_per_s": 64 / (ms / 1e3),
-                                    "gpix_per_s": pix / (ms / 1e3) / 1e9, "nnz_total": nnz,
-                                    "algorithmic_gbs": ab / (ms / 1e3) / 1e9}
-    del plan, igs, imgs
+    out["batching_64_instances"] = batching_workload(torch, dev, gen)
 
     # 4096 frames of 2167 x 2070 uint32 through one matrix (2000 q bins): a 256-frame device
     # buffer integrated 16 times
@@ -461,6 +473,12 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only_batching:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        print(json.dumps({"batching_instances": batching_workload(torch, dev, gen, args.steps,
+                                                                  args.instances)}))
+        return
 
     from paper_1412_6367_gb300 import api, synth
     w = synth.pilatus_workload()
