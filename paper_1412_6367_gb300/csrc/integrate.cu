@@ -670,8 +670,18 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
         }
     } else {
         int k = 0;
+        // a CTA's items (every gridDim.x-th) mostly stay in one instance for many rounds:
+        // the instance's parameters are looked up again only when the item leaves its range
+        ConsumerParams cp = consumer_params(single);
+        int64_t cur_begin = 0, cur_end = multi ? 0 : n_items;
         for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x, ++k) {
             const int s = k % S, n = k / S;
+            if (item < cur_begin || item >= cur_end) {
+                const Inst &d = inst_of(single, multi, n_inst, item);
+                cp = consumer_params(d);
+                cur_begin = d.item_begin;
+                cur_end = d.item_begin + d.n_items;
+            }
             bool ok = mbar_wait_bounded(&full[s], (uint32_t)(n & 1));
             ok = __all_sync(0xffffffffu, ok);
             if (__any_sync(0xffffffffu, !ok || *abort_flag != 0)) {  // warp-uniform decision
@@ -681,8 +691,6 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
                 }
                 break;
             }
-            const ConsumerParams cp = multi ? consumer_params(inst_of(single, multi, n_inst, item))
-                                            : consumer_params(single);
             consume_dispatch<AT, WT, MODE, NIMG, DT>(cp, smem + (size_t)s * sg.stage_bytes, sg, &ctr[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
