@@ -636,19 +636,27 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
     if (warp < kProducers) {
         int k = 0;
         int64_t item = blockIdx.x;
+        // the instance of the current and of the next item, searched for again only when an
+        // item leaves the range of the last one found
+        const Inst *dc = &single, *dn = &single;
+        auto find = [&](int64_t it, const Inst *hint) -> const Inst * {
+            if (!multi || (it >= hint->item_begin && it < hint->item_begin + hint->n_items)) return hint;
+            return &inst_of(single, multi, n_inst, it);
+        };
         TileDesc td{};
         if (item < n_items) {
-            const Inst &d0 = inst_of(single, multi, n_inst, item);
-            td = load_desc(d0, item - d0.item_begin);
+            if (multi) dc = dn = &inst_of(single, multi, n_inst, item);
+            td = load_desc(*dc, item - dc->item_begin);
         }
         for (; item < n_items; item += gridDim.x, ++k) {
             const int s = k % S, n = k / S;
             // prefetch the next item's descriptor while this one is staged
             const int64_t next = item + gridDim.x;
             TileDesc tn{};
+            dc = dn;
             if (next < n_items) {
-                const Inst &dn = inst_of(single, multi, n_inst, next);
-                tn = load_desc(dn, next - dn.item_begin);
+                dn = find(next, dc);
+                tn = load_desc(*dn, next - dn->item_begin);
             }
             bool ok = true;
             if (n > 0) ok = mbar_wait_bounded(&empty[s], (uint32_t)((n - 1) & 1));
@@ -663,8 +671,7 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
                 asm volatile("cp.async.wait_all;" ::: "memory");
                 break;
             }
-            const Inst &d = inst_of(single, multi, n_inst, item);
-            produce<MODE, WT, TMA>(d, tm, item - d.item_begin, td, smem + (size_t)s * sg.stage_bytes,
+            produce<MODE, WT, TMA>(*dc, tm, item - dc->item_begin, td, smem + (size_t)s * sg.stage_bytes,
                                    sg, &full[s], &ctr[s], warp);
             td = tn;
         }
