@@ -389,6 +389,20 @@ int az_integrate_lut(az_integrator *h, const void *image_dev, int image_dtype, c
  * sets it to whichever layout integrates one frame faster.  AZ_EINVAL for another value. */
 int az_set_layout(az_integrator *h, int layout);
 
+/* ---- failure detection ------------------------------------------------------------------ */
+
+/*
+ * Self-test of the bounded device-side wait (no counterpart in the paper).  Every staged
+ * kernel of the library waits on shared-memory barriers with a bound, after which it records
+ * AZ_ETIMEOUT in a status word and returns instead of hanging.  This launches one warp that
+ * waits, with a bound of limit_cycles SM clock cycles (1 .. 2e9, about one second), on a
+ * barrier that nothing completes (arrive == 0) or that the warp's first thread completes
+ * first (arrive != 0), then writes the outcome to *out_status (host int): AZ_ETIMEOUT or
+ * AZ_OK.  Synchronises `stream`; the context stays usable.  AZ_EINVAL for a NULL status
+ * or a bound outside the range, before any launch.
+ */
+int az_selftest_wait(int arrive, int64_t limit_cycles, int *out_status, az_stream_t stream);
+
 /* ---- kernel timing --------------------------------------------------------------------- */
 
 /* Per-kernel totals recorded while profiling is enabled.  Kinds: 0 = phase-1 frames kernel

@@ -86,6 +86,7 @@ SIGNATURES = {
     "az_lut_export": ([vp, vp, vp, vp, vp], i32),
     "az_integrate_lut": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "az_set_layout": ([vp, i32], i32),
+    "az_selftest_wait": ([i32, ctypes.c_int64, vp, vp], i32),
     "az_profile_enable": ([vp, i32], i32),
     "az_set_copy_engine": ([vp, i32], i32),
     "az_profile_read": ([vp, ctypes.POINTER(Profile)], i32),

@@ -419,6 +419,16 @@ class Integrator:
         self.refresh_info()
 
 
+def selftest_wait(arrive=False, limit_cycles=2_000_000, device=None):
+    """Run the bounded-wait self-test (az_selftest_wait) on the current CUDA device; returns
+    the status the kernel wrote: 0 (AZ_OK) or -7 (AZ_ETIMEOUT)."""
+    lib = L.load()
+    st = ctypes.c_int(1)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    check(lib.az_selftest_wait(1 if arrive else 0, int(limit_cycles), ctypes.byref(st), _stream(dev)))
+    return st.value
+
+
 class MultiPlan:
     """Several integrators of uneven shape in one persistent launch (az_multi_create)."""
 

@@ -221,6 +221,9 @@ extern "C" int az_integrator_status(az_integrator *h) {
 extern "C" void az_integrator_destroy(az_integrator *h) {
     if (!h) return;
     cudaDeviceSynchronize();
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    for (cudaEvent_t e : h->copy_events)
+        if (e) cudaEventDestroy(e);
     delete h;
 }
 
@@ -339,18 +342,19 @@ extern "C" int az_integrate_batch_host(az_integrator *h, const void *frames_host
         oi[b] = reinterpret_cast<float *>(fr[b] + chunk * fbytes);
         os[b] = oi[b] + (size_t)chunk * h->nrows;
     }
-    cudaStream_t cp = nullptr;
-    cudaEvent_t start = nullptr, up[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
     int rc = AZ_OK;
     auto ck = [&](cudaError_t e) {
         if (e != cudaSuccess && rc == AZ_OK) rc = fail(AZ_ECUDA, "az_integrate_batch_host: %s", cudaGetErrorString(e));
     };
-    ck(cudaStreamCreateWithFlags(&cp, cudaStreamNonBlocking));
-    ck(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    for (int b = 0; b < 2; ++b) {
-        ck(cudaEventCreateWithFlags(&up[b], cudaEventDisableTiming));
-        ck(cudaEventCreateWithFlags(&done[b], cudaEventDisableTiming));
-    }
+    // the upload stream and its events live with the integrator (created once)
+    if (!h->copy_stream) ck(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t &e : h->copy_events)
+        if (!e) ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    if (rc != AZ_OK) return rc;
+    cudaStream_t cp = h->copy_stream;
+    cudaEvent_t start = h->copy_events[0];
+    cudaEvent_t up[2] = {h->copy_events[1], h->copy_events[2]};
+    cudaEvent_t done[2] = {h->copy_events[3], h->copy_events[4]};
     if (rc == AZ_OK) {
         ck(cudaEventRecord(start, s));
         ck(cudaStreamWaitEvent(cp, start, 0));
@@ -383,12 +387,6 @@ extern "C" int az_integrate_batch_host(az_integrator *h, const void *frames_host
     }
     ck(cudaStreamSynchronize(s));
     ck(cudaStreamSynchronize(cp));
-    if (cp) cudaStreamDestroy(cp);
-    if (start) cudaEventDestroy(start);
-    for (int b = 0; b < 2; ++b) {
-        if (up[b]) cudaEventDestroy(up[b]);
-        if (done[b]) cudaEventDestroy(done[b]);
-    }
     h->last_stream = s;
     return rc;
 }

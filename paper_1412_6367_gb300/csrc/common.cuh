@@ -181,6 +181,8 @@ struct az_integrator {
     int layout = AZ_LAYOUT_TILED;  // what az_integrate1d/2d use
     // host copies for the end-to-end path
     azint::DevBuf host_stage;  // device frames buffer for az_integrate_batch_host
+    cudaStream_t copy_stream = nullptr;          // its upload stream, created on first use
+    cudaEvent_t copy_events[5] = {};             // start, uploaded[2], consumed[2]
     cudaStream_t last_stream = nullptr;
     mutable azint::Profiler prof;
 };
@@ -298,11 +300,12 @@ __device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *bar, uint32_t parit
 // Bounded wait on an mbarrier phase: gives up (returns false) after about two seconds of
 // the SM's clock, however long each suspended try lasts.
 constexpr long long kWaitLimitCycles = 4000000000LL;
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  long long limit = kWaitLimitCycles) {
     if (mbar_try_wait_hint(bar, parity, 1000000u)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait_hint(bar, parity, 1000000u))
-        if (clock64() - t0 > kWaitLimitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 

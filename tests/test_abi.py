@@ -65,3 +65,15 @@ def test_host_only_lut_calls():
     assert L.az_integrate_lut(None, None, 0, None, None, None, None, 1, None, None, None, None, None) == -1
     assert L.az_set_layout(None, 1) == -1
     assert b"az_set_layout" in L.az_last_error()
+
+
+def test_selftest_wait_rejects_bad_arguments_on_host():
+    """The bounded-wait self-test checks its arguments before any launch."""
+    import ctypes as C
+    from paper_1412_6367_gb300 import _lib
+    L = _lib.load()
+    st = C.c_int(5)
+    assert L.az_selftest_wait(0, 1000, None, None) == -1
+    assert L.az_selftest_wait(0, 0, C.byref(st), None) == -1
+    assert L.az_selftest_wait(0, 3_000_000_000, C.byref(st), None) == -1
+    assert st.value == 5
