@@ -377,6 +377,34 @@ def batching_workload(torch, dev, gen, reps=10, n=64):
     return res
 
 
+def size_sweep(torch, dev, gen):
+    """One int32 frame per call (tiled and look-up-table layouts, FP32) and 32-frame batches
+    at the paper's benchmark sizes (1 to 16 Mpixel, bounding-box split, 1000 q bins):
+    ms per frame and Mpixel/s."""
+    from paper_1412_6367_gb300 import api, synth
+    res = []
+    for w in synth.size_sweep_workloads():
+        g = api.Geometry(*w.geometry.astuple())
+        ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "bbox", device=dev)
+        frames = torch.randint(0, 4000, (32, w.ny, w.nx), generator=gen, device=dev, dtype=torch.int32)
+        row = {"shape": [w.ny, w.nx], "nnz": ig.info["nnz"]}
+        for layout in ("tiled", "lut"):
+            ig.set_layout(layout)
+            for _ in range(3):
+                ig.integrate(frames[0], precision="fp32")
+            row[layout + "_single_ms"] = _event_ms(torch, lambda: ig.integrate(frames[0], precision="fp32"), 10)
+        ig.set_layout("tiled")
+        for _ in range(2):
+            ig.integrate_batch(frames)
+        row["batched_ms_per_frame"] = _event_ms(torch, lambda: ig.integrate_batch(frames), 3) / 32
+        npix = w.ny * w.nx
+        row["mpix_per_s"] = {k: npix / (row[k] / 1e3) / 1e6 for k in
+                             ("tiled_single_ms", "lut_single_ms", "batched_ms_per_frame")}
+        res.append(row)
+        del frames, ig
+    return res
+
+
 def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     """The other workloads' throughput (device-resident inputs, warm), reported beside the
     headline: the 2D cake, the 64-instance persistent launch, a 4096-frame stream through
@@ -435,6 +463,7 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     lut["tiled_fp32_ms_per_frame"] = out["pilatus_single_frame_fp32"]["ms_per_frame"]
     out["pilatus_single_frame_lut"] = lut
     out["pilatus1m_stages"] = stage_breakdown(torch, dev)
+    out["size_sweep_1_to_16_mpix"] = size_sweep(torch, dev, gen)
 
     # propagated Poisson variance of the bin sums, 64 Pilatus frames per call
     fr64 = img.view(torch.int32).unsqueeze(0).expand(64, -1, -1).contiguous().view(torch.uint32)

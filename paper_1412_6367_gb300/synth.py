@@ -90,6 +90,23 @@ def pilatus1m_workload(seed: int = 1, split: int = SPLIT_BBOX, npt: int = 1000) 
                     image_dtype="int32", masked=True, corrections=True, seed=seed)
 
 
+SWEEP_SHAPES = ((1024, 1024), (1448, 1448), (2048, 2048), (2527, 2463), (3456, 3456), (4096, 4096))
+
+
+def size_sweep_workloads(npt: int = 1000):
+    """The image sizes of the paper's benchmarks (Sec. 6: 1, 2, 4, 6, 12 and 16 Mpixel):
+    square detectors of 1024^2, 1448^2, 2048^2, 3456^2 and 4096^2 pixels and the Pilatus-6M
+    shape, int32 counts, 100 um pixels, 100 mm, beam centred, no tilt, q in nm^-1, `npt`
+    bins, bounding-box split (the split of those benchmarks), no mask, no corrections."""
+    out = []
+    for ny, nx in SWEEP_SHAPES:
+        g = GeometryParams(dist=0.1, poni1=ny * 100e-6 / 2, poni2=nx * 100e-6 / 2,
+                           pixel1=100e-6, pixel2=100e-6, wavelength=1.0e-10)
+        out.append(Workload("sweep-%dx%d-bbox-%d" % (ny, nx, npt), ny, nx, g, UNIT_Q_NM, SPLIT_BBOX,
+                            npt, image_dtype="int32"))
+    return out
+
+
 def cake_workload(seed: int = 2) -> Workload:
     """2048 x 2048 float32, 50 um, 150 mm, rot1 = 0.05, PONI at the detector centre (a pixel
     corner), 500 2theta x 360 chi bins, full split, corrections as the Pilatus case."""
