@@ -52,6 +52,9 @@ def parse(argv=None):
     ap.add_argument("--only-batching", action="store_true",
                     help="run only the many-instance launch (3 warm-up + --steps launches) "
                          "and print its figures")
+    ap.add_argument("--only-single", action="store_true",
+                    help="run only one Pilatus-6M frame per call (FP32, corrections; 3 warm-up "
+                         "+ --steps calls) and print its time")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the many-instance launch with --only-batching")
     return ap.parse_args(argv)
@@ -350,6 +353,25 @@ def stage_breakdown(torch, dev, reps=20):
     return res
 
 
+def single_frame_workload(torch, dev, reps=20):
+    """One Pilatus-6M uint32 frame per call, FP32 compensated, with dark, flat, solid angle
+    and polarisation: ms per frame."""
+    from paper_1412_6367_gb300 import api, synth
+    w = synth.pilatus_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    mask = synth.pilatus_module_mask(w.ny, w.nx)
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "full", mask=mask, device=dev)
+    crad, _ = g.positions(w.ny, w.nx, "q_nm^-1", "centres", chi=False, device=dev)
+    img = torch.from_numpy(synth.ring_image(crad.cpu().numpy(), seed=3).view(np.int32)).to(dev)
+    img = img.view(torch.uint32)
+    dark, flat = (torch.from_numpy(a).to(dev) for a in synth.dark_flat(w.ny, w.nx, w.seed))
+    sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
+    for _ in range(3):
+        ig.integrate(img, dark, flat, sa, pol, precision="fp32")
+    ms = _event_ms(torch, lambda: ig.integrate(img, dark, flat, sa, pol, precision="fp32"), reps)
+    return {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
+
+
 def batching_workload(torch, dev, gen, reps=10, n=64):
     """n (default 64) heterogeneous instances (three detector shapes, 500 / 2000 / 5000 q
     bins, full split) in one graph-captured persistent launch: ms per launch and throughput."""
@@ -502,6 +524,9 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only_single:
+        print(json.dumps({"pilatus_single_frame_fp32": single_frame_workload(torch, dev, args.steps)}))
+        return
     if args.only_batching:
         gen = torch.Generator(device=dev)
         gen.manual_seed(7)

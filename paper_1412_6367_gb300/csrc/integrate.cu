@@ -1058,8 +1058,16 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
         int k = 0, issued = 0;  // items seen, items whose entries were issued
         uint32_t j = 0;         // plane stages issued
         bool stop = false;
+        // descriptors are read two items ahead: with one or two frame groups per item the
+        // producer would otherwise wait for a descriptor from DRAM on every item
+        TileDesc ahead[2] = {};
+        for (int u = 0; u < 2; ++u)
+            if (blockIdx.x + u * gridDim.x < (unsigned)a.n_tiles) ahead[u] = fr_desc(a, blockIdx.x + u * gridDim.x);
         for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x, ++k) {
-            const TileDesc td = fr_desc(a, item);
+            const TileDesc td = ahead[0];
+            ahead[0] = ahead[1];
+            const int64_t far = (int64_t)item + 2 * (int64_t)gridDim.x;
+            if (far < a.n_tiles) ahead[1] = fr_desc(a, (int)far);
             const int eb = k % NE;
             bool ok = true;
             if (k >= NE) ok = mbar_wait_bounded(&eempty[eb], (uint32_t)(((k / NE) - 1) & 1));
@@ -1484,9 +1492,15 @@ bool fr_geom(const az_integrator *h, int G, int dk, int n_groups, FrGeom &fg) {
     fg.nstages = (int)std::min<int64_t>(kFrMaxStages, avail > 0 ? avail / per : 0);
     fg.nebufs = 2;
     if (n_groups <= 2 && fg.nstages >= 2) {
-        fg.nstages = 2;
-        const int64_t left = avail - 2 * per;
-        fg.nebufs = 2 + (int)std::min<int64_t>(kFrMaxEbufs - 2, left / (int64_t)fg.ebuf_bytes);
+        // every item takes n_groups plane stages: grow both rings together, so that as many
+        // items are in flight for their planes as for their entries
+        for (int e = 2; e <= kFrMaxEbufs; ++e) {
+            const int ns = std::min(kFrMaxStages, std::max(2, n_groups * e));
+            const int64_t need = (int64_t)e * fg.ebuf_bytes + (int64_t)ns * per + kFrFixedBytes;
+            if (need > (int64_t)max_smem_per_block()) break;
+            fg.nebufs = e;
+            fg.nstages = ns;
+        }
     }
     return fg.nstages >= 2;
 }
