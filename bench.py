@@ -207,9 +207,10 @@ def ncu_traffic():
     sha = frames_kernel_sha()
     m = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
     t = re.search(r"traffic_bytes_per_launch_full:\s*([0-9.e+]+)", text)
-    if not m or not t or m.group(1) != sha:
+    f = re.search(r"capture_frames_per_launch:\s*([0-9]+)", text)
+    if not m or not t or not f or m.group(1) != sha:
         return None
-    return float(t.group(1))
+    return float(t.group(1)), int(f.group(1))
 
 
 def cpu_baseline(w, seconds, check=None):
@@ -603,10 +604,15 @@ def main():
     per_launch_frames = B * args.steps / max(n_launch, 1)
     ab = phase1_frames_bytes(info["nnz"], info["n_unmasked"], per_launch_frames)
     achieved = ab / (tot_ms / max(n_launch, 1) / 1e3) / 1e9 if n_launch else None
-    traffic_full = ncu_traffic()
+    # DRAM bytes of one launch from the committed capture; a capture of another launch size
+    # is scaled by frames (approximate: the matrix part does not grow with the frames)
+    cap = ncu_traffic()
+    traffic_full = None
+    if cap:
+        traffic_full = cap[0] * (per_launch_frames / cap[1] if cap[1] != int(per_launch_frames) else 1.0)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
-                "traffic": (traffic_full * per_launch_frames / 64.0) if traffic_full else None,
+                "traffic": traffic_full,
                 "kernel": "frames_kernel<G=%d,U32,dark> (frames pass, %d frames per launch)" % (
                     info["frames_per_pass"], int(per_launch_frames)),
                 "algorithmic_bytes_per_launch": ab, "peak_source": peak_kind + " hbm_gbs",

@@ -29,7 +29,7 @@ __global__ void fill_frames_kernel(uint32_t *out, int64_t n, uint32_t seed) {
 int alloc_scratch(az_integrator *h) {
     const size_t nseg = (size_t)std::max(h->tl.nseg, 1);
     const size_t single = 3 * nseg * sizeof(double);
-    const size_t frames = 64 * nseg * sizeof(float);
+    const size_t frames = (size_t)kMaxFramesPerLaunch * nseg * sizeof(float);
     h->partial_bytes = std::max(single, frames);
     AZ_TRY(h->partial.alloc(h->partial_bytes));
     AZ_TRY(h->norm.alloc(sizeof(float) * 2 * (size_t)h->nrows));

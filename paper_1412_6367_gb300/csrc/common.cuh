@@ -152,6 +152,10 @@ struct ProfScope {
 };
 }  // namespace azint
 
+// Frames one launch of the batched forward covers (its per-segment partial sums are kept
+// for all of them): the matrix is read once per launch.
+constexpr int kMaxFramesPerLaunch = 64;
+
 struct az_integrator {
     int device = 0;
     int ny = 0, nx = 0, npt_rad = 0, npt_azim = 0, nrows = 0, unit = 0, split = 0;

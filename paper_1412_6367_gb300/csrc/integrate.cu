@@ -1806,8 +1806,8 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
                                 rec_words_of(h), stage_e, ent_dk);
     const int eng = engine_for(h);
     if (eng == AZ_COPY_TMA) {
-        // tile-resident entries (frames_kernel), up to 64 frames per launch
-        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+        // tile-resident entries (frames_kernel), up to kMaxFramesPerLaunch frames per launch
+        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, kMaxFramesPerLaunch));
         for (int f0 = 0; f0 < n; f0 += chunk) {
             const int nf = std::min(chunk, n - f0);
             Inst d = make_inst(h, false);
@@ -1892,7 +1892,7 @@ int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, cons
         ent_dk = L.ent_dark.as<float>();
     }
     const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(L.nseg, 1)));
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, kMaxFramesPerLaunch));
     for (int f0 = 0; f0 < n; f0 += chunk) {
         const int nf = std::min(chunk, n - f0);
         Inst d = make_inst(h, false);
@@ -1910,12 +1910,12 @@ int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, cons
 }
 
 // Propagated variance of the signal sums, V = sum w^2 max(img, 0), for n frames through the
-// frames kernel (chunks of up to 64 frames), written to oV [n][nrows].
+// frames kernel (chunks of up to kMaxFramesPerLaunch frames), written to oV [n][nrows].
 int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float *oV, cudaStream_t s) {
     if (engine_for(h) != AZ_COPY_TMA)
         return fail(AZ_EUNSUPPORTED, "az_integrate_variance: needs the tensor-copy engine (tiles up to 220 pixels wide)");
     const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(h->tl.nseg, 1)));
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, 64));
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, kMaxFramesPerLaunch));
     for (int f0 = 0; f0 < n; f0 += chunk) {
         const int nf = std::min(chunk, n - f0);
         Inst d = make_inst(h, false);
