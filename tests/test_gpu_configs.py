@@ -165,3 +165,25 @@ def test_differentiation_full_size(pilatus, pilatus_gpu, precision):
     for got, ref in ((img.grad, gi_ref), (flat.grad, gf_ref)):
         per, norm = rel_err(got.double().cpu().numpy(), ref)
         assert norm <= 1e-5, (precision, per, norm)
+
+
+def test_largest_size_flat_image():
+    """The largest image of the size sweep (4096 x 4096 int32, 1000 q bins, bounding-box
+    split): a flat image of ones integrates to I = 1 exactly in every bin with counts, through
+    the batch, the single-frame and the look-up-table forms, and the counts add up to the
+    pixel count (every pixel's weights sum to 1)."""
+    w = synth.size_sweep_workloads()[-1]
+    assert (w.ny, w.nx) == (4096, 4096)
+    g = gpu_geometry(w.geometry)
+    ig = api().Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, UNIT_NAMES[w.unit], SPLIT_NAMES[w.split])
+    ones = torch.ones((3, w.ny, w.nx), dtype=torch.int32, device="cuda")
+    out = ig.integrate_batch(ones)
+    one = ig.integrate(ones[0], precision="fp32")
+    lut = ig.integrate_lut(ones[0], precision="fp32")
+    C = out.count.cpu().numpy()
+    has = C > 0
+    for I in (out.I[0], out.I[2], one.I, lut.I):
+        I = I.cpu().numpy()
+        assert np.all(I[has] == 1.0) and np.all(I[~has] == 0.0)
+    assert abs(float(out.count.double().sum()) - w.ny * w.nx) <= 1e-6 * w.ny * w.nx
+    assert ig.status() == 0
