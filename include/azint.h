@@ -177,8 +177,11 @@ void az_integrator_destroy(az_integrator *h);
  *   N_b = sum_p A_bp flat_p solid_angle_p pol_p  (out_sum_norm)
  *   C_b = sum_p A_bp                             (out_count)
  *   I_b = S_b / N_b, 0 where N_b == 0            (out_I)
- * in one fused pass: the cast of the image (Sec. 6.4 "cast"), the corrections ("correction")
- * and the reduction ("integrate") run in the same kernel and no output needs zeroing.
+ * with no output zeroing (Sec. 6.4's "memset").  FP64: one fused pass, the cast of the image
+ * (Sec. 6.4 "cast"), the corrections ("correction") and the reduction ("integrate") in one
+ * kernel.  FP32: a pixel pass forms cast(img) - dark and flat * solid_angle * polarization,
+ * which the batched kernel then reduces (the bits of that frame in any batch); C is kept per
+ * layout.  With az_set_layout(AZ_LAYOUT_LUT) both go through the look-up table instead.
  * image_dev: device [ny][nx] of image_dtype.  dark/flat/solid_angle/polarization: device
  * float [ny][nx], each may be NULL (dark = 0, the others = 1).  precision AZ_PREC_FP64:
  * FP64 weights and accumulation, outputs are device double[nrows]; AZ_PREC_FP32_COMP:
@@ -251,8 +254,8 @@ int az_integrate_batch(az_integrator *h, const void *frames_dev, int n_frames,
  * [n_frames][nrows], out_count device float [nrows] (any may be NULL).  FP32 compensated;
  * computed with the weights divided by each pixel's flat * solid_angle * polarization once
  * per call.  Through the batched kernel (tensor-copy engine; AZ_EUNSUPPORTED for tiles
- * wider than 220 pixels).  With no flat, solid angle or polarisation the result equals
- * az_integrate_batch's I and S bit for bit.
+ * wider than 236 pixels or with AZ_COPY_ASYNC).  With no flat, solid angle or polarisation
+ * the result equals az_integrate_batch's I and S bit for bit.
  */
 int az_integrate_batch_pixelnorm(az_integrator *h, const void *frames_dev, int n_frames,
                                  int image_dtype, const float *dark, const float *flat,
@@ -267,7 +270,7 @@ int az_integrate_batch_pixelnorm(az_integrator *h, const void *frames_dev, int n
  * V_b = sum_p A_bp^2 max(img_p, 0); the standard error of I_b is sqrt(V_b) / N_b.
  * frames device [n_frames][ny][nx]; out_sum_variance device float [n_frames][nrows].
  * FP32 compensated, through the batched kernel (tensor-copy engine; AZ_EUNSUPPORTED for
- * tiles wider than 220 pixels).
+ * tiles wider than 236 pixels or with AZ_COPY_ASYNC).
  */
 int az_integrate_variance(az_integrator *h, const void *frames_dev, int n_frames,
                           int image_dtype, float *out_sum_variance, az_stream_t stream);

@@ -1854,7 +1854,7 @@ int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, cons
                     const float *flat, const float *sa, const float *pol, float *oI, float *oU,
                     float *oC, cudaStream_t s) {
     if (engine_for(h) != AZ_COPY_TMA || h->partial_bytes < 2 * sizeof(float) * (size_t)h->tl.nseg)
-        return fail(AZ_EUNSUPPORTED, "az_integrate_batch_pixelnorm: needs the tensor-copy engine (tiles up to 220 pixels wide)");
+        return fail(AZ_EUNSUPPORTED, "az_integrate_batch_pixelnorm: needs the tensor-copy engine (tiles up to 236 pixels wide)");
     TiledLayout &L = h->tl;
     const int64_t npix = (int64_t)h->ny * h->nx;
     const int nrows = h->nrows;
@@ -1913,7 +1913,7 @@ int batch_pixelnorm(az_integrator *h, const void *frames, int n, int dtype, cons
 // frames kernel (chunks of up to kMaxFramesPerLaunch frames), written to oV [n][nrows].
 int batch_variance(az_integrator *h, const void *frames, int n, int dtype, float *oV, cudaStream_t s) {
     if (engine_for(h) != AZ_COPY_TMA)
-        return fail(AZ_EUNSUPPORTED, "az_integrate_variance: needs the tensor-copy engine (tiles up to 220 pixels wide)");
+        return fail(AZ_EUNSUPPORTED, "az_integrate_variance: needs the tensor-copy engine (tiles up to 236 pixels wide)");
     const int64_t cap = (int64_t)(h->partial_bytes / (sizeof(float) * (size_t)std::max(h->tl.nseg, 1)));
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(cap, kMaxFramesPerLaunch));
     for (int f0 = 0; f0 < n; f0 += chunk) {
