@@ -52,6 +52,9 @@ def parse(argv=None):
     ap.add_argument("--only-batching", action="store_true",
                     help="run only the many-instance launch (3 warm-up + --steps launches) "
                          "and print its figures")
+    ap.add_argument("--only-cake", action="store_true",
+                    help="run only the 2048 x 2048 cake batch (64 frames; 3 warm-up + --steps "
+                         "calls) and print its rate")
     ap.add_argument("--only-single", action="store_true",
                     help="run only one Pilatus-6M frame per call (FP32, corrections; 3 warm-up "
                          "+ --steps calls) and print its time")
@@ -354,6 +357,27 @@ def stage_breakdown(torch, dev, reps=20):
     return res
 
 
+def cake_workload(torch, dev, gen, reps=5):
+    """2048 x 2048 float32 frames, 500 2theta x 360 chi bins, full split, corrections:
+    64-frame batches and one frame per call."""
+    from paper_1412_6367_gb300 import api, synth
+    w = synth.cake_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, w.npt_azim, "2th_deg", "full", device=dev)
+    dark = torch.rand((w.ny, w.nx), generator=gen, device=dev) + 10.0
+    flat = 0.95 + 0.1 * torch.rand((w.ny, w.nx), generator=gen, device=dev)
+    sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
+    frames = 1000.0 * torch.rand((64, w.ny, w.nx), generator=gen, device=dev)
+    for _ in range(3):
+        ig.integrate_batch(frames, dark, flat, sa, pol)
+    ms = _event_ms(torch, lambda: ig.integrate_batch(frames, dark, flat, sa, pol), reps)
+    ms1 = _event_ms(torch, lambda: ig.integrate(frames[0], dark, flat, sa, pol, precision="fp32"), 10)
+    res = {"batched_frames_per_s": 64 / (ms / 1e3), "single_frame_fp32_ms": ms1,
+           "nnz": ig.info["nnz"]}
+    del frames, ig
+    return res
+
+
 def single_frame_workload(torch, dev, reps=20):
     """One Pilatus-6M uint32 frame per call, FP32 compensated, with dark, flat, solid angle
     and polarisation: ms per frame."""
@@ -437,21 +461,7 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     gen = torch.Generator(device=dev)
     gen.manual_seed(7)
 
-    # cake: 2048 x 2048 float32, 500 x 360 bins, full split, corrections
-    w = synth.cake_workload()
-    g = api.Geometry(*w.geometry.astuple())
-    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, w.npt_azim, "2th_deg", "full", device=dev)
-    dark = torch.rand((w.ny, w.nx), generator=gen, device=dev) + 10.0
-    flat = 0.95 + 0.1 * torch.rand((w.ny, w.nx), generator=gen, device=dev)
-    sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
-    frames = 1000.0 * torch.rand((64, w.ny, w.nx), generator=gen, device=dev)
-    for _ in range(3):
-        ig.integrate_batch(frames, dark, flat, sa, pol)
-    ms = _event_ms(torch, lambda: ig.integrate_batch(frames, dark, flat, sa, pol), 5)
-    ms1 = _event_ms(torch, lambda: ig.integrate(frames[0], dark, flat, sa, pol, precision="fp32"), 10)
-    out["cake_2048x2048_500x360"] = {"batched_frames_per_s": 64 / (ms / 1e3),
-                                      "single_frame_fp32_ms": ms1, "nnz": ig.info["nnz"]}
-    del frames, ig
+    out["cake_2048x2048_500x360"] = cake_workload(torch, dev, gen)
 
     out["batching_64_instances"] = batching_workload(torch, dev, gen)
 
@@ -525,6 +535,11 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.only_cake:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        print(json.dumps({"cake_2048x2048_500x360": cake_workload(torch, dev, gen, args.steps)}))
+        return
     if args.only_single:
         print(json.dumps({"pilatus_single_frame_fp32": single_frame_workload(torch, dev, args.steps)}))
         return
