@@ -368,12 +368,15 @@ def cake_workload(torch, dev, gen, reps=5):
     flat = 0.95 + 0.1 * torch.rand((w.ny, w.nx), generator=gen, device=dev)
     sa, pol = g.solid_angle(w.ny, w.nx, device=dev), g.polarization(w.ny, w.nx, 0.99, device=dev)
     frames = 1000.0 * torch.rand((64, w.ny, w.nx), generator=gen, device=dev)
+    default = (ig.info["tile_h"], ig.info["tile_w"], ig.info["frames_per_pass"])
+    ig.autotune(16)  # setup, untimed: tiles and frames per pass for this matrix
     for _ in range(3):
         ig.integrate_batch(frames, dark, flat, sa, pol)
     ms = _event_ms(torch, lambda: ig.integrate_batch(frames, dark, flat, sa, pol), reps)
     ms1 = _event_ms(torch, lambda: ig.integrate(frames[0], dark, flat, sa, pol, precision="fp32"), 10)
     res = {"batched_frames_per_s": 64 / (ms / 1e3), "single_frame_fp32_ms": ms1,
-           "nnz": ig.info["nnz"]}
+           "nnz": ig.info["nnz"], "default_tuning": default,
+           "autotuned": (ig.info["tile_h"], ig.info["tile_w"], ig.info["frames_per_pass"])}
     del frames, ig
     return res
 
@@ -472,9 +475,12 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "full", device=dev)
     buf = torch.randint(0, 4000, (256, w.ny, w.nx), generator=gen, device=dev, dtype=torch.int32)
     fr = buf.view(torch.uint32)
+    ig.autotune(16)  # setup, untimed
     ig.integrate_batch(fr[:64])
     ms = _event_ms(torch, lambda: ig.integrate_batch(fr), 16)
-    out["stream_4096x2167x2070"] = {"frames_per_s": 256 / (ms / 1e3), "ms_per_4096": 16 * ms}
+    out["stream_4096x2167x2070"] = {"frames_per_s": 256 / (ms / 1e3), "ms_per_4096": 16 * ms,
+                                     "autotuned": (ig.info["tile_h"], ig.info["tile_w"],
+                                                   ig.info["frames_per_pass"])}
     del buf, fr, ig
 
     # one Pilatus frame per call through the single-frame path (FP32 compensated)

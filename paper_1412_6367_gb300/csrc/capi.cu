@@ -38,8 +38,9 @@ int alloc_scratch(az_integrator *h) {
 }
 
 int finish_build(az_integrator *h, cudaStream_t s) {
-    // defaults measured on the Pilatus-6M workload; az_autotune refines them per matrix
-    int th = 8, tw = 224;
+    // defaults measured on the Pilatus-6M workload (1D) and the 2048 x 2048 cake (2D, whose
+    // bins are compact in both directions); az_autotune refines them per matrix
+    int th = h->npt_azim > 0 ? 32 : 8, tw = h->npt_azim > 0 ? 64 : 224;
     if (build_tiled_layout(h, th, tw, s) != AZ_OK) {  // a denser matrix: smaller tiles
         th = 8;
         tw = 64;
