@@ -433,7 +433,8 @@ int az_profile_read(az_integrator *h, az_profile *out);
  * one class are 16 * width bytes apart, which meets the tensor-map stride rule for any
  * width); it applies to tiles up to 236 pixels wide, wider tiles use AZ_COPY_ASYNC.
  * AZ_COPY_ASYNC issues 16-byte cp.async copies spread over the producer warps.  Results are
- * identical; only speed differs.  Defaults: 8 x 224 pixel tiles, 8 frames per pass. */
+ * identical; only speed differs.  Defaults: 8 x 224 pixel tiles (32 x 64 for 2D integrators),
+ * 8 frames per pass. */
 int az_set_copy_engine(az_integrator *h, int engine);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
