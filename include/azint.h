@@ -210,6 +210,10 @@ int az_integrate2d(const az_integrator *h, const void *image_dev, int image_dtyp
  * allocations (which can block and synchronise the device) once set-up is over.  The
  * integrator itself must have been built beforehand.
  *
+ * It always runs the tiled single-pass form (the one-launch reduction of FP64 frames, for
+ * both precisions), whatever az_set_layout chose, so its FP32 bits may differ from
+ * az_integrate1d's by rounding order (both within the stated tolerances).
+ *
  * The partial sums the forward keeps between its two kernels go to one fixed array of
  * AZ_NOALLOC_SCRATCH_BYTES compiled into this library; every GPU that loads the library holds
  * that memory until the process exits.  A call needs 3 * segments * 8 bytes (FP64) or
