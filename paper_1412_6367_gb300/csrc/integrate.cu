@@ -1,20 +1,28 @@
 // Fused correction + sparse matrix-vector product (Sec. 5.2, Sec. 6.4) on the pixel-tiled
-// layout, in two deterministic launches:
+// layout.  Every form ends with the same deterministic phase 2; phase 1 comes in two kernels:
 //
-//   phase 1 (persistent): each CTA walks a static round-robin list of work items (an active
-//     pixel tile, and for many frames a group of frames).  Warp 0 bulk-copies (TMA,
-//     cp.async.bulk + mbarrier) the tile's rows of every needed plane -- image frames,
-//     dark, flat, solid angle, polarisation -- and the tile's matrix entries into one of two
-//     shared-memory stages while the CTA reduces the previous item from the other stage.
-//     Groups of 32/R lanes each reduce one matrix row ("segment") of the tile from shared
-//     memory, R rows per warp, and write one partial sum per (segment, plane).
-//   phase 2: one warp per (row, frame) sums the row's partials in a fixed order and forms
+//   frames_kernel (persistent, one CTA per SM): a work item is a pixel tile (or a piece of
+//     a heavy one) for every frame of the launch.  One producer warp copies the item's
+//     record and entries (location, weight, per-entry dark) once into a ring of entry
+//     buffers and streams the tile's pixels, G frames at a time, into a ring of plane stages
+//     (bulk and tensor TMA, mbarrier-tracked, every wait bounded); 16 consumer warps give
+//     lanes (segment, frame) pairs and write one partial sum per (segment, frame).  It serves
+//     batches, the frame-independent sums N and C, the propagated variance, the per-pixel-
+//     corrected form and single FP32 frames (after single_planes_kernel forms the corrected
+//     frame and its normalisation per pixel).
+//   phase1_kernel (persistent): one item per tile with all planes of one frame (image, dark,
+//     flat, solid angle, polarisation) and the tile's entries in a ring of stages; four
+//     lanes per segment form S, N and C.  It serves FP64 frames, the many-instance launch,
+//     the allocation-free entry point and the cp.async copy engine.
+//   phase 2: per (row, frame), the row's segment partials summed in a fixed order; then
 //     S, N, C and I = S / N.
 //
-// Casting the image, subtracting the dark, forming flat * solid angle * polarisation and
-// the reduction happen in the same pass (the paper's separate cast / correction / memset /
-// integrate kernels).  FP32 sums are Kahan-compensated (Sec. 5.2.2); FP64 sums are plain.
-// No atomics are used, so results are bit-reproducible run to run.
+// Where a segment is one matrix row's entries inside one tile.  The image cast, the dark
+// and flat * solid angle * polarisation are applied inside these kernels or in one per-pixel
+// pass (the paper runs separate cast / correction / memset / integrate kernels).  FP32 sums
+// are Kahan-compensated (Sec. 5.2.2); FP64 sums are plain.  No atomics touch the sums, so
+// results are bit-reproducible run to run, and a frame gives the same bits alone or in any
+// batch.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
