@@ -1,6 +1,8 @@
 // C ABI of the library: argument validation, handle lifetime, error strings, build
-// orchestration, the end-to-end host-buffer path and the tuner.  All device work is done by
-// the kernels in geometry.cu, csr_build.cu, integrate.cu and backward.cu.
+// orchestration, the end-to-end host-buffer path and the tuner.  The device work is done by
+// the kernels in geometry.cu, csr_build.cu, integrate.cu, lut.cu and backward.cu (the
+// allocation-free entry point and the wait self-test have their own files); the only kernel
+// here fills the tuner's synthetic frames.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
