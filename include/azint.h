@@ -215,18 +215,23 @@ int az_integrate2d(const az_integrator *h, const void *image_dev, int image_dtyp
  * az_integrate1d's by rounding order (both within the stated tolerances).
  *
  * The partial sums the forward keeps between its two kernels go to one fixed array of
- * AZ_NOALLOC_SCRATCH_BYTES compiled into this library; every GPU that loads the library holds
- * that memory until the process exits.  A call needs 3 * segments * 8 bytes (FP64) or
+ * AZ_NOALLOC_SCRATCH_BYTES compiled into this library; every GPU on which an integrator is
+ * built holds that memory from then until the process exits.  A call needs 3 * segments * 8 bytes (FP64) or
  * 3 * segments * 4 bytes (FP32 compensated), segments = az_info.n_segments; a larger need is
  * refused with AZ_ESHAPE and a message giving both sizes.  Nothing in the array has to start
  * at zero: each call writes every partial sum it later reads.
  *
  * All calls on a device share the array and it keeps the last call's contents, so calls
  * that overlap on the GPU (different streams, or host threads without ordering) race and
- * give wrong results: order them on one stream.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Arguments, outputs and errors are otherwise those of
- * az_integrate1d.
+ * give wrong results: order them on one stream.  Building an integrator on a device (the
+ * set-up) looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current) and loads the kernels this call runs; under the CUDA runtime's lazy module
+ * loading (the default) that is when the array's memory is reserved on that device, so the
+ * calls themselves take none.  A call made with a device current on which no integrator was
+ * built does that look-up itself: make such a first call before any stream capture.  If a
+ * bounded device-side wait gives up during a call (az_integrator_status then reports
+ * AZ_ETIMEOUT), that call's outputs are not valid: they may hold sums left in the array by
+ * an earlier call.  Arguments, outputs and errors are otherwise those of az_integrate1d.
  */
 #define AZ_NOALLOC_SCRATCH_BYTES (8u << 20)
 int az_integrate_noalloc(const az_integrator *h, const void *image_dev, int image_dtype,

@@ -54,7 +54,8 @@ int finish_build(az_integrator *h, cudaStream_t s) {
     AZ_TRY(h->status.alloc(sizeof(int)));
     AZ_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), s));
     AZ_CUDA(cudaStreamSynchronize(s));
-    return AZ_OK;
+    // the allocation-free entry point's fixed array and kernels, loaded at set-up
+    return noalloc_setup();
 }
 
 int check_build_args(int ny, int nx, int npt_rad, int npt_azim, int unit, int split) {

@@ -216,6 +216,9 @@ int forward_single(const az_integrator *h, const void *image, int dtype, const f
 int forward_single_into(const az_integrator *h, const void *image, int dtype, const float *dark,
                         const float *flat, const float *sa, const float *pol, int precision,
                         void *oI, void *oS, void *oN, void *oC, void *partial, cudaStream_t s);
+int preload_single_pass();
+// set-up of the allocation-free entry point on the current device (noalloc.cu)
+int noalloc_setup();
 int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
                   const float *flat, const float *sa, const float *pol, float *oI, float *oS,
                   float *oN, float *oC, cudaStream_t s);

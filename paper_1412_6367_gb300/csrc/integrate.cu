@@ -1702,6 +1702,30 @@ int forward_single(const az_integrator *h, const void *image, int dtype, const f
 
 // forward_single with the per-segment partial sums in a buffer the caller supplies (at least
 // 3 * nseg values of the accumulation type) instead of the integrator's own; no profiling.
+// Loads, without launching them, the kernels forward_single_into can launch (both
+// precisions, every image type, both copy engines, and phase 2).  Under the CUDA runtime's
+// lazy loading a kernel's code is otherwise loaded, and may take device memory, at its first
+// launch.
+template <class K> int preload_kernel(K k) {
+    cudaFuncAttributes fa;
+    AZ_CUDA(cudaFuncGetAttributes(&fa, k));
+    return AZ_OK;
+}
+template <class AT, int DT> int preload_single_dt() {
+    AZ_TRY(preload_kernel(phase1_kernel<AT, AT, MODE_SINGLE, 1, DT, true>));
+    return preload_kernel(phase1_kernel<AT, AT, MODE_SINGLE, 1, DT, false>);
+}
+int preload_single_pass() {
+    AZ_TRY((preload_single_dt<double, AZ_DTYPE_F32>()));
+    AZ_TRY((preload_single_dt<double, AZ_DTYPE_U32>()));
+    AZ_TRY((preload_single_dt<double, AZ_DTYPE_I32>()));
+    AZ_TRY((preload_single_dt<float, AZ_DTYPE_F32>()));
+    AZ_TRY((preload_single_dt<float, AZ_DTYPE_U32>()));
+    AZ_TRY((preload_single_dt<float, AZ_DTYPE_I32>()));
+    AZ_TRY(preload_kernel(phase2_kernel<double, MODE_SINGLE>));
+    return preload_kernel(phase2_kernel<float, MODE_SINGLE>);
+}
+
 int forward_single_into(const az_integrator *h, const void *image, int dtype, const float *dark,
                         const float *flat, const float *sa, const float *pol, int precision,
                         void *oI, void *oS, void *oN, void *oC, void *partial, cudaStream_t s) {

@@ -41,6 +41,18 @@ bool aligned4(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0
 
 }  // namespace
 
+namespace azint {
+// Set-up on the current device, run when an integrator is built there: the array's address
+// is looked up (under the CUDA runtime's lazy module loading this is what loads this file's
+// module and reserves the array) and the kernels of the single-pass forward are loaded, so
+// that the entry point's calls themselves take no device memory.
+int noalloc_setup() {
+    void *p = nullptr;
+    AZ_TRY(scratch_address(&p));
+    return preload_single_pass();
+}
+}  // namespace azint
+
 extern "C" int az_integrate_noalloc(const az_integrator *h, const void *image_dev, int image_dtype,
                                     const float *dark, const float *flat, const float *solid_angle,
                                     const float *polarization, int precision, void *out_I,

@@ -131,6 +131,34 @@ def test_batching_64_instances():
     assert len(checked_shapes) == 3
 
 
+def test_batching_instances_with_corrections():
+    """The many-instance launch with dark, flat, solid angle and polarisation per instance:
+    every (shape, bin count) pair of the 64-instance workload is checked against the oracle
+    per bin, and every instance against its own single-frame FP32 integration."""
+    ws = synth.batch_instances()
+    pairs = {}
+    for k, w in enumerate(ws):
+        pairs.setdefault((w.ny, w.nx, w.npt_rad), k)
+    sel = sorted(pairs.values())
+    cases, gpus, imgs, corrs = [], [], [], []
+    for k in sel:
+        c = Case(ws[k], with_corrections=True)
+        cases.append(c)
+        gpus.append(c.gpu_from_geometry())
+        imgs.append(c.image_dev())
+        corrs.append(c.corrections_dev())
+    plan = api().MultiPlan(gpus, imgs, darks=[x[0] for x in corrs], flats=[x[1] for x in corrs],
+                           solid_angles=[x[2] for x in corrs], polarizations=[x[3] for x in corrs])
+    outs = plan.launch(use_graph=True)
+    outs = plan.launch(use_graph=True)
+    torch.cuda.synchronize()
+    for c, g, img, corr, o in zip(cases, gpus, imgs, corrs, outs):
+        check(o, c.oracle(), "fp32", "instance %s" % c.w.name)
+        one = g.integrate(img, *corr, precision="fp32")
+        check(o, [t.double().cpu().numpy() for t in one], "fp32", "single %s" % c.w.name)
+        assert g.status() == 0
+
+
 def test_stream_through_one_matrix_from_host():
     w = synth.stream_workload()
     c = Case(w, with_corrections=False)
@@ -165,6 +193,19 @@ def test_differentiation_full_size(pilatus, pilatus_gpu, precision):
     for got, ref in ((img.grad, gi_ref), (flat.grad, gf_ref)):
         per, norm = rel_err(got.double().cpu().numpy(), ref)
         assert norm <= 1e-5, (precision, per, norm)
+    # pixel by pixel: the transpose product of the GPU forward's own I and N (the upstream
+    # gradient 2 (I - T) changes sign between bins, so each pixel is bounded by the tolerance
+    # times its sum over absolute values)
+    res = pilatus_gpu.integrate(img.detach(), dark, flat.detach(), sa, pol, precision=precision)
+    Ig, Ng = (t.double().cpu().numpy() for t in (res.I, res.sum_norm))
+    gg = 2.0 * (Ig - T)
+    gi_ref, gf_ref = O.backward(c.A, gg, Ig, Ng, c.sa, c.pol)
+    gi_abs, gf_abs = O.backward(c.A, np.abs(gg), np.abs(Ig), Ng, c.sa, c.pol)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for got, ref, absref in ((img.grad, gi_ref, gi_abs), (flat.grad, gf_ref, gf_abs)):
+        got = got.double().cpu().numpy().ravel()
+        bad = np.abs(got - ref) > tol * np.abs(absref) + 1e-300
+        assert not bad.any(), (precision, int(bad.sum()))
 
 
 def test_largest_size_flat_image():

@@ -63,6 +63,54 @@ def test_no_split_counts_match_numpy_histogram(seed):
         assert np.abs(counts - hist).sum() <= 2 * amb.sum()
 
 
+def _centres_scipy(g, ny, nx):
+    """Pixel-centre 2theta (degrees) and chi (degrees in [-180, 180)) computed here with
+    scipy's rotation, independently of the oracle: t = R (d1 - poni1, d2 - poni2, L),
+    2theta = atan2(|t_12|, t3), chi = atan2(t1, t2) (Sec. 3 coordinate list)."""
+    R = Rotation.from_euler("xyz", [g.rot1, g.rot2, g.rot3]).as_matrix()
+    d1 = (np.arange(ny) + 0.5)[:, None] * g.pixel1 - g.poni1
+    d2 = (np.arange(nx) + 0.5)[None, :] * g.pixel2 - g.poni2
+    v = np.stack(np.broadcast_arrays(d1, d2, np.full((1, 1), g.dist)), axis=-1)
+    t = v @ R.T
+    tth = np.degrees(np.arctan2(np.hypot(t[..., 0], t[..., 1]), t[..., 2]))
+    chi = np.degrees(np.arctan2(t[..., 0], t[..., 1]))
+    chi = np.where(chi >= 180.0, chi - 360.0, chi)  # the chi range is [-180, 180)
+    return tth, chi
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_no_split_2d_counts_match_numpy_histogram2d(seed):
+    """The 2D histogram form of Sec. 3.3: with no splitting a pixel goes whole into the bin
+    of its centre (radial bin from the data range, chi bin of 360 / npt_azim degrees from
+    -180).  Counts per (chi, radial) bin equal numpy.histogram2d of the same centre values,
+    except where a value lies within 4 ulp of a bin edge in either direction."""
+    rng = np.random.default_rng(40 + seed)
+    ny, nx = 60, 72
+    npt, nch = int(rng.integers(10, 120)), int(rng.choice([4, 36, 90, 360]))
+    g = _geom(synth.random_geometry(rng, ny, nx))
+    tth, chi = _centres_scipy(g, ny, nx)
+    mask = (rng.random((ny, nx)) < 0.1).astype(np.uint8)
+    A = O.csr_build(ny, nx, tth, chi, mask, npt, nch, O.SPLIT_NONE)
+    sel = mask == 0
+    x, c = tth[sel], chi[sel]
+    hist, ce, xe = np.histogram2d(c, x, bins=[nch, npt], range=[[-180.0, 180.0], [x.min(), x.max()]])
+    counts = np.diff(A.indptr).reshape(nch, npt)  # row = chi_bin * npt + radial_bin
+    assert A.lo == x.min() and A.hi == x.max()
+    assert np.all(A.data == 1.0)
+    amb = _ambiguous(x, xe) | _ambiguous(c, ce)
+    if not amb.any():
+        assert np.array_equal(counts, hist)
+    else:
+        assert np.abs(counts - hist).sum() <= 2 * amb.sum()
+    # each pixel's entry: its own (chi, radial) bin, independently of the histogram's edges
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.indptr))
+    kr = np.minimum(np.floor((tth.ravel() - x.min()) / ((x.max() - x.min()) / npt)), npt - 1)
+    kc = np.floor((chi.ravel() + 180.0) / (360.0 / nch)).astype(np.int64) % nch
+    want = (kc * npt + kr.astype(np.int64))[A.indices]
+    ok = (want == rows) | np.concatenate([amb, [False]])[np.searchsorted(np.flatnonzero(sel), A.indices)]
+    assert ok.all()
+
+
 def test_no_split_equals_naive_loop_mean():
     """Sec. 3.2: per bin, the mean of the pixels whose radius lies in [r1, r2)."""
     p = synth.tiny_workload().geometry

@@ -3,7 +3,8 @@ memory while they run (a plugin whose host program's memory pool has reserved th
 acquisition loop that forbids allocations after set-up).  Its partial sums live in a fixed
 array inside the library instead of the integrator's own buffer, so it must give what
 az_integrate1d / az_integrate2d give, call after call, with the array keeping whatever the
-previous call left in it.
+previous call left in it -- and the calls themselves must leave the device's free memory
+unchanged.
 
 This file is collected last on purpose: if it fails, a run that stops at the first failure
 has already run every other test."""
@@ -12,7 +13,7 @@ import pytest
 import torch
 
 from paper_1412_6367_gb300 import synth
-from gpu_common import Case, api, gpu_geometry, needs_gpu, small_workload, to_dev
+from gpu_common import Case, api, gpu_geometry, needs_gpu, rel_err, small_workload, to_dev
 
 pytestmark = [pytest.mark.gpu, needs_gpu]
 
@@ -46,15 +47,24 @@ def test_noalloc_matches_integrate_two_calls(precision, npt_azim):
     # two different frames, one after the other: the second call runs on whatever the
     # first one left in the library's fixed array
     frames = [case.image, synth.ring_image(case.crad, seed=12, dtype=np.uint32)]
-    for img in frames:
-        dimg = to_dev(img)
-        ref = ig.integrate(dimg, *corr, precision=precision)
-        got = ig.integrate_noalloc(dimg, *corr, precision=precision,
-                                   out=_outputs(ig, precision))
-        torch.cuda.synchronize()
-        shape = ref.I.shape
-        got = [t.view(shape) for t in got]
-        _close(got, ref, TOL[precision])
+    dimgs = [to_dev(img) for img in frames]
+    refs = [ig.integrate(d, *corr, precision=precision) for d in dimgs]
+    outs = [_outputs(ig, precision) for _ in frames]
+    torch.cuda.synchronize()
+    # everything the calls read or write exists now: the calls themselves allocate nothing
+    free0 = torch.cuda.mem_get_info()[0]
+    alloc0 = torch.cuda.memory_allocated()
+    got = [ig.integrate_noalloc(d, *corr, precision=precision, out=o) for d, o in zip(dimgs, outs)]
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    for img, g, ref in zip(frames, got, refs):
+        g = [t.view(ref.I.shape) for t in g]
+        _close(g, ref, TOL[precision])
+        # and per bin against the oracle
+        for name, gg, oo in zip("ISNC", g, case.oracle(img)):
+            per, norm = rel_err(gg.double().cpu().numpy(), oo)
+            assert per <= TOL[precision] and norm <= TOL[precision], (name, per, norm)
     assert ig.status() == 0
 
 
