@@ -160,6 +160,26 @@ int az_integrator_info(const az_integrator *h, az_info *out);
 int az_csr_export(const az_integrator *h, int32_t *indptr_host, int32_t *indices_host,
                   double *data_host);
 
+/*
+ * A new integrator from a bins x pixels matrix in host memory, in the scipy-compatible CSR form
+ * that az_csr_export writes (Sec. 5.2.1): indptr int32[nrows + 1] (indptr[0] = 0, non-
+ * decreasing), indices int32[nnz] (pixel ids p = i * nx + j < ny * nx, strictly ascending
+ * within a row), data double[nnz] (finite weights), nrows = npt_rad (npt_azim == 0) or
+ * npt_azim * npt_rad (row = chi_bin * npt_rad + rad_bin).  lo < hi is the radial range the
+ * bins cover (az_radial_axis gives lo + (k + 1/2) (hi - lo) / npt_rad); unit and split are
+ * kept as labels only (az_integrator_info).  Lets a matrix built elsewhere -- another
+ * program's, a stored one, or a reference implementation's -- be applied by this library's
+ * kernels.  The matrix is checked on the host, then copied to the device and laid out as
+ * az_csr_build's (pixel-major CSC for the adjoint, tiled layout for the forward), so
+ * az_csr_export of the result returns the three arrays bit for bit.  Synchronises `stream`.
+ * Errors, before any device work: AZ_EINVAL (NULL arrays, indptr or indices out of order or
+ * range, non-finite weight, lo >= hi, bad enums), AZ_ESHAPE (ny, nx < 1), AZ_ERANGE (no
+ * entries); afterwards AZ_ENOMEM or AZ_ECUDA.
+ */
+int az_csr_import(int ny, int nx, int npt_rad, int npt_azim, int unit, int split,
+                  const int32_t *indptr_host, const int32_t *indices_host, const double *data_host,
+                  double lo, double hi, az_stream_t stream, az_integrator **out);
+
 /* Radial bin centres lo + (k + 1/2) delta, k < npt_rad, into host double[npt_rad]. */
 int az_radial_axis(const az_integrator *h, double *out_host);
 
@@ -253,6 +273,30 @@ int az_integrate_batch(az_integrator *h, const void *frames_dev, int n_frames,
                        const float *solid_angle, const float *polarization, float *out_I,
                        float *out_sum_signal, float *out_sum_norm, float *out_count,
                        az_stream_t stream);
+
+/*
+ * Bind the correction arrays of a detector to the integrator once (Sec. 6.4 names dark, flat,
+ * solid-angle and polarisation corrections; they do not change from frame to frame): the
+ * frame-independent part of az_integrate_batch -- the dark of every matrix entry's pixel, and
+ * per bin N = sum w flat solid_angle pol and C = sum w -- is formed now, on `stream`, into
+ * buffers the integrator owns.  The arrays (device float [ny][nx], any may be NULL: dark = 0,
+ * the others = 1) are not read again: later changes to them take effect only when they are
+ * bound again.  A new binding replaces the old one; a change of the tiled layout
+ * (az_set_tuning, az_autotune) drops it.  Errors: those of az_integrate_batch's arguments.
+ */
+int az_set_corrections(az_integrator *h, const float *dark, const float *flat,
+                       const float *solid_angle, const float *polarization, az_stream_t stream);
+
+/*
+ * az_integrate_batch with the corrections bound by az_set_corrections: frames device
+ * [n_frames][ny][nx]; out_I, out_sum_signal device float [n_frames][nrows]; out_sum_norm,
+ * out_count device float [nrows] receive the bound N and C (each may be NULL).  The bits equal
+ * az_integrate_batch's with the same corrections.  AZ_EINVAL when nothing is bound or the
+ * layout changed since the binding.
+ */
+int az_integrate_batch_bound(az_integrator *h, const void *frames_dev, int n_frames,
+                             int image_dtype, float *out_I, float *out_sum_signal,
+                             float *out_sum_norm, float *out_count, az_stream_t stream);
 
 /*
  * The paper's own normalisation (Sec. 6.4: a correction pass, then the integration, whose

@@ -66,6 +66,7 @@ SIGNATURES = {
     "az_csr_build_from_positions": ([i32, i32, vp, vp, i32, i32, i32, vp, vp, PP], i32),
     "az_integrator_info": ([vp, ctypes.POINTER(Info)], i32),
     "az_csr_export": ([vp, vp, vp, vp], i32),
+    "az_csr_import": ([i32, i32, i32, i32, i32, i32, vp, vp, vp, f64, f64, vp, PP], i32),
     "az_radial_axis": ([vp, vp], i32),
     "az_integrator_status": ([vp], i32),
     "az_integrator_destroy": ([vp], None),
@@ -74,6 +75,8 @@ SIGNATURES = {
     "az_integrate_noalloc": ([vp, vp, i32, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], i32),
     "az_integrate_batch": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_batch_host": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp], i32),
+    "az_set_corrections": ([vp, vp, vp, vp, vp, vp], i32),
+    "az_integrate_batch_bound": ([vp, vp, i32, i32, vp, vp, vp, vp, vp], i32),
     "az_integrate_variance": ([vp, vp, i32, i32, vp, vp], i32),
     "az_integrate_batch_pixelnorm": ([vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp], i32),
     "az_integrate_backward": ([vp, vp, vp, vp, vp, vp, i32, vp, vp, vp], i32),

@@ -148,6 +148,24 @@ class Integrator:
         return cls(h, device)
 
     @classmethod
+    def from_csr(cls, shape, indptr, indices, data, npt_rad, npt_azim=0, lo=0.0, hi=1.0,
+                 unit="2th_deg", split="full", device="cuda"):
+        """Import a host CSR matrix (scipy layout: indptr, indices, data) of nrows = npt_rad
+        (1D) or npt_azim * npt_rad rows over ny * nx pixels (az_csr_import); lo, hi is the
+        radial range of the bins."""
+        ny, nx = shape
+        lib = L.load()
+        ip = np.ascontiguousarray(indptr, dtype=np.int32)
+        ix = np.ascontiguousarray(indices, dtype=np.int32)
+        dv = np.ascontiguousarray(data, dtype=np.float64)
+        h = ctypes.c_void_p()
+        check(lib.az_csr_import(ny, nx, npt_rad, npt_azim, _code(UNITS, unit, "unit"),
+                                _code(SPLITS, split, "split"), ctypes.c_void_p(ip.ctypes.data),
+                                ctypes.c_void_p(ix.ctypes.data), ctypes.c_void_p(dv.ctypes.data),
+                                float(lo), float(hi), _stream(device), ctypes.byref(h)))
+        return cls(h, device)
+
+    @classmethod
     def from_positions(cls, shape, rad, chi, npt_rad, npt_azim=0, split="bbox", mask=None):
         """Build from FP64 positions (device tensors): centres for split 'none', corners
         otherwise (az_csr_build_from_positions)."""
@@ -272,6 +290,32 @@ class Integrator:
             _dev(out.I, "I", torch.float32), _dev(out.sum_signal, "S", torch.float32),
             _dev(out.sum_norm, "N", torch.float32), _dev(out.count, "C", torch.float32),
             _stream(dev)))
+        return out
+
+    def set_corrections(self, dark=None, flat=None, solid_angle=None, polarization=None):
+        """Bind the correction arrays once (az_set_corrections): per-entry darks, N and C are
+        formed now and reused by integrate_batch_bound."""
+        dev = next((t.device for t in (dark, flat, solid_angle, polarization) if t is not None),
+                   self.device)
+        check(self._lib.az_set_corrections(self._h, *self._corr(dark, flat, solid_angle, polarization),
+                                           _stream(dev)))
+
+    def integrate_batch_bound(self, frames, out=None):
+        """Frames [n, ny, nx] through the corrections bound by set_corrections
+        (az_integrate_batch_bound).  Returns (I [n, nrows], S [n, nrows], N [nrows], C [nrows])."""
+        n = frames.shape[0]
+        npix = self.info["ny"] * self.info["nx"]
+        fr = _dev(frames, "frames", numel=n * npix)
+        dev = frames.device
+        if out is None:
+            out = Result(torch.empty((n, self.nrows), dtype=torch.float32, device=dev),
+                         torch.empty((n, self.nrows), dtype=torch.float32, device=dev),
+                         torch.empty(self.nrows, dtype=torch.float32, device=dev),
+                         torch.empty(self.nrows, dtype=torch.float32, device=dev))
+        check(self._lib.az_integrate_batch_bound(
+            self._h, fr, n, image_dtype_code(frames), _dev(out.I, "I", torch.float32),
+            _dev(out.sum_signal, "S", torch.float32), _dev(out.sum_norm, "N", torch.float32),
+            _dev(out.count, "C", torch.float32), _stream(dev)))
         return out
 
     def integrate_pixelnorm(self, frames, dark=None, flat=None, solid_angle=None, polarization=None):

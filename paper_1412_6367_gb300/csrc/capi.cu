@@ -162,6 +162,56 @@ extern "C" int az_csr_build_from_positions(int ny, int nx, const double *rad_dev
                         npt_rad, npt_azim, -1, split, mask_dev, (cudaStream_t)stream, out);
 }
 
+extern "C" int az_csr_import(int ny, int nx, int npt_rad, int npt_azim, int unit, int split,
+                             const int32_t *indptr_host, const int32_t *indices_host,
+                             const double *data_host, double lo, double hi, az_stream_t stream,
+                             az_integrator **out) {
+    clear_error();
+    const char *who = "az_csr_import";
+    if (!out || !indptr_host) return fail(AZ_EINVAL, "%s: NULL argument", who);
+    *out = nullptr;
+    AZ_TRY(check_build_args(ny, nx, npt_rad, npt_azim, unit, split));
+    if (!(std::isfinite(lo) && std::isfinite(hi) && lo < hi))
+        return fail(AZ_EINVAL, "%s: the radial range [%g, %g] must be finite with lo < hi", who, lo, hi);
+    // the whole matrix is checked on the host before any device work
+    const int nrows = npt_azim > 0 ? npt_rad * npt_azim : npt_rad;
+    const int64_t npix = (int64_t)ny * nx;
+    if (indptr_host[0] != 0) return fail(AZ_EINVAL, "%s: indptr[0] must be 0", who);
+    for (int r = 0; r < nrows; ++r)
+        if (indptr_host[r + 1] < indptr_host[r])
+            return fail(AZ_EINVAL, "%s: indptr decreases at row %d", who, r);
+    const int64_t nnz = indptr_host[nrows];
+    if (nnz == 0) return fail(AZ_ERANGE, "%s: the matrix has no entries", who);
+    if (!indices_host || !data_host) return fail(AZ_EINVAL, "%s: NULL indices or data", who);
+    for (int r = 0; r < nrows; ++r)
+        for (int32_t k = indptr_host[r]; k < indptr_host[r + 1]; ++k) {
+            const int32_t p = indices_host[k];
+            if (p < 0 || p >= npix)
+                return fail(AZ_EINVAL, "%s: entry %d of row %d has pixel %d outside [0, %lld)", who, (int)k, r,
+                            (int)p, (long long)npix);
+            if (k > indptr_host[r] && p <= indices_host[k - 1])
+                return fail(AZ_EINVAL, "%s: the pixels of row %d are not strictly ascending", who, r);
+            if (!std::isfinite(data_host[k]))
+                return fail(AZ_EINVAL, "%s: entry %d has a non-finite weight", who, (int)k);
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    az_integrator *h = new (std::nothrow) az_integrator;
+    if (!h) return fail(AZ_ENOMEM, "%s: out of host memory", who);
+    cudaGetDevice(&h->device);
+    h->ny = ny; h->nx = nx; h->npt_rad = npt_rad; h->npt_azim = npt_azim; h->nrows = nrows;
+    h->unit = unit; h->split = split; h->nnz = nnz;
+    h->lo = lo; h->hi = hi; h->delta = (hi - lo) / npt_rad;
+    int rc = import_csr(h, indptr_host, indices_host, data_host, s);
+    if (rc == AZ_OK) rc = finish_build(h, s);
+    if (rc != AZ_OK) {
+        cudaStreamSynchronize(s);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return AZ_OK;
+}
+
 extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
     clear_error();
     if (!h || !out) return fail(AZ_EINVAL, "az_integrator_info: NULL argument");
@@ -184,7 +234,8 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
                             &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
                             &h->tl.norm_frames, &h->tl.ent_wnorm, &h->lut32, &h->lut64,
-                            &h->lut_vals, &h->lut_part, &h->one_planes};
+                            &h->lut_vals, &h->lut_part, &h->one_planes, &h->bound_ent_dark,
+                            &h->bound_norm};
     int64_t tot = 0;
     for (const DevBuf *b : bufs) tot += (int64_t)b->bytes;
     out->device_bytes = tot;
@@ -293,6 +344,30 @@ extern "C" int az_integrate_batch(az_integrator *h, const void *frames_dev, int 
     return forward_batch(h, frames_dev, n_frames, image_dtype, dark, flat, solid_angle,
                          polarization, out_I, out_sum_signal, out_sum_norm, out_count,
                          (cudaStream_t)stream);
+}
+
+extern "C" int az_set_corrections(az_integrator *h, const float *dark, const float *flat,
+                                  const float *solid_angle, const float *polarization,
+                                  az_stream_t stream) {
+    clear_error();
+    static const uint32_t no_frames = 0;
+    AZ_TRY(check_forward(h, &no_frames, AZ_DTYPE_F32, dark, flat, solid_angle, polarization,
+                         "az_set_corrections"));
+    h->last_stream = (cudaStream_t)stream;
+    return bind_corrections(h, dark, flat, solid_angle, polarization, (cudaStream_t)stream);
+}
+
+extern "C" int az_integrate_batch_bound(az_integrator *h, const void *frames_dev, int n_frames,
+                                        int image_dtype, float *out_I, float *out_sum_signal,
+                                        float *out_sum_norm, float *out_count, az_stream_t stream) {
+    clear_error();
+    if (n_frames < 0) return fail(AZ_ESHAPE, "az_integrate_batch_bound: n_frames < 0");
+    static const uint32_t no_frames = 0;
+    AZ_TRY(check_forward(h, n_frames == 0 ? &no_frames : frames_dev, image_dtype, nullptr, nullptr,
+                         nullptr, nullptr, "az_integrate_batch_bound"));
+    h->last_stream = (cudaStream_t)stream;
+    return forward_batch_bound(h, frames_dev, n_frames, image_dtype, out_I, out_sum_signal, out_sum_norm,
+                               out_count, (cudaStream_t)stream);
 }
 
 extern "C" int az_integrate_batch_pixelnorm(az_integrator *h, const void *frames_dev, int n_frames,

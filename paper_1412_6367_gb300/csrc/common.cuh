@@ -183,6 +183,10 @@ struct az_integrator {
     azint::DevBuf one_planes;
     int64_t lut_width = 0;
     int layout = AZ_LAYOUT_TILED;  // what az_integrate1d/2d use
+    // corrections bound by az_set_corrections: per-entry darks, N and C of the current layout
+    bool corr_bound = false, corr_dark = false;
+    azint::DevBuf bound_ent_dark;  // float [padded_nnz]
+    azint::DevBuf bound_norm;      // float [2][nrows]: N, C
     // host copies for the end-to-end path
     azint::DevBuf host_stage;  // device frames buffer for az_integrate_batch_host
     cudaStream_t copy_stream = nullptr;          // its upload stream, created on first use
@@ -203,6 +207,8 @@ int build_integrator(int ny, int nx, const double *rad, const double *chi, int n
                      int npt_azim, int unit, int split, const uint8_t *mask, cudaStream_t s,
                      az_integrator *h);
 int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s);
+int import_csr(az_integrator *h, const int32_t *indptr, const int32_t *indices, const double *data,
+               cudaStream_t s);
 
 // scan / sort primitives (csr_build.cu)
 int exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
@@ -242,7 +248,12 @@ int forward_batch_one(az_integrator *h, const void *image, int dtype, const floa
 int batch_norm(az_integrator *h, const float *flat, const float *sa, const float *pol, float *oN,
                float *oC, cudaStream_t s);
 int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
-                 float *oI, float *oS, int frame_out0, cudaStream_t s);
+                 float *oI, float *oS, int frame_out0, cudaStream_t s,
+                 const float *ent_dark_given = nullptr, const float *norm = nullptr);
+int bind_corrections(az_integrator *h, const float *dark, const float *flat, const float *sa,
+                     const float *pol, cudaStream_t s);
+int forward_batch_bound(az_integrator *h, const void *frames, int n, int dtype, float *oI, float *oS,
+                        float *oN, float *oC, cudaStream_t s);
 int max_smem_per_block();
 
 // ------------------------------------------------------------------------------------

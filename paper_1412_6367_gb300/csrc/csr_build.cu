@@ -627,6 +627,16 @@ __global__ void csr_rows_kernel(const int32_t *__restrict__ ptr, int nrows, int6
     }
 }
 
+// Pixels with at least one entry (column pointers ptr[npix + 1]).
+__global__ void nonempty_kernel(const int32_t *__restrict__ ptr, int64_t n, int *__restrict__ count) {
+    int c = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x)
+        c += ptr[p + 1] > ptr[p];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
 struct TileGeom {
     int nx, th, tw, srow, ss, ntx;
 };
@@ -1008,9 +1018,51 @@ int build_integrator(int ny, int nx, const double *rad, const double *chi, int n
     return AZ_OK;
 }
 
+// The integrator's matrix from a host CSR (already checked by the caller): the CSR copied to
+// the device, the pixel-major CSC formed by a stable sort of the entries by pixel (so each
+// pixel's entries keep ascending row order), and the count of pixels that have entries.
+int import_csr(az_integrator *h, const int32_t *indptr, const int32_t *indices, const double *data,
+               cudaStream_t s) {
+    const int64_t npix = (int64_t)h->ny * h->nx, nnz = h->nnz;
+    AZ_TRY(h->csr_ptr.alloc(sizeof(int32_t) * (h->nrows + 1)));
+    AZ_TRY(h->csr_idx.alloc(sizeof(int32_t) * nnz));
+    AZ_TRY(h->csr_w64.alloc(sizeof(double) * nnz));
+    AZ_CUDA(cudaMemcpyAsync(h->csr_ptr.p, indptr, sizeof(int32_t) * (h->nrows + 1), cudaMemcpyHostToDevice, s));
+    AZ_CUDA(cudaMemcpyAsync(h->csr_idx.p, indices, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, s));
+    AZ_CUDA(cudaMemcpyAsync(h->csr_w64.p, data, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    DevBuf rows, keys, perm, cnt, nonempty;
+    AZ_TRY(rows.alloc(sizeof(int32_t) * nnz));
+    AZ_TRY(keys.alloc(sizeof(uint32_t) * nnz));
+    AZ_TRY(perm.alloc(sizeof(int32_t) * nnz));
+    AZ_TRY(launch_gs(csr_rows_kernel, nnz, s, h->csr_ptr.as<int32_t>(), h->nrows, nnz, rows.as<int32_t>()));
+    AZ_TRY(launch_gs(to_u32_kernel, nnz, s, h->csr_idx.as<int32_t>(), keys.as<uint32_t>(), nnz));
+    AZ_TRY(launch_gs(iota_kernel, nnz, s, perm.as<int32_t>(), nnz));
+    AZ_TRY(stable_sort_pairs(keys.as<uint32_t>(), perm.as<int32_t>(), nnz, bits_for(npix - 1), s));
+    AZ_TRY(h->csc_ptr.alloc(sizeof(int32_t) * (npix + 1)));
+    AZ_TRY(h->csc_row.alloc(sizeof(int32_t) * nnz));
+    AZ_TRY(h->csc_w64.alloc(sizeof(double) * nnz));
+    AZ_TRY(h->csc_w32.alloc(sizeof(float) * nnz));
+    AZ_TRY(launch_gs(csr_gather_kernel, nnz, s, perm.as<int32_t>(), rows.as<int32_t>(), h->csr_w64.as<double>(),
+                     h->csc_row.as<int32_t>(), h->csc_w64.as<double>(), nnz));
+    AZ_TRY(launch_gs(f64_to_f32_kernel, nnz, s, h->csc_w64.as<double>(), h->csc_w32.as<float>(), nnz));
+    AZ_TRY(cnt.alloc(sizeof(int32_t) * npix));
+    AZ_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * npix, s));
+    AZ_TRY(launch_gs(count_keys_kernel, nnz, s, h->csr_idx.as<int32_t>(), nnz, cnt.as<int32_t>()));
+    AZ_TRY(exclusive_scan_i32(cnt.as<int32_t>(), h->csc_ptr.as<int32_t>(), npix, s));
+    AZ_TRY(nonempty.alloc(sizeof(int)));
+    AZ_CUDA(cudaMemsetAsync(nonempty.p, 0, sizeof(int), s));
+    AZ_TRY(launch_gs(nonempty_kernel, npix, s, h->csc_ptr.as<int32_t>(), npix, nonempty.as<int>()));
+    int n_unmasked = 0;
+    AZ_CUDA(cudaMemcpyAsync(&n_unmasked, nonempty.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    AZ_CUDA(cudaStreamSynchronize(s));
+    h->n_unmasked = n_unmasked;
+    return AZ_OK;
+}
+
 int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     TiledLayout &L = h->tl;
     h->count_ready = false;  // the accumulation order of C depends on the layout
+    h->corr_bound = false;   // bound corrections are per layout too (entry order, sums)
     const int64_t nnz = h->nnz;
     if (th < 4 || (th % 4) != 0 || tw < 4 || (tw % 4) != 0)
         return fail(AZ_EINVAL, "tile %dx%d: both sides must be positive multiples of 4", th, tw);

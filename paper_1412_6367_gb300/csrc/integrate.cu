@@ -1806,11 +1806,13 @@ int batch_norm(az_integrator *h, const float *flat, const float *sa, const float
 }
 
 int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const float *dark,
-                 float *oI, float *oS, int frame_out0, cudaStream_t s) {
+                 float *oI, float *oS, int frame_out0, cudaStream_t s, const float *ent_dark_given,
+                 const float *norm) {
     // the dark of every entry, in entry order, so that the frames pass reads it with the
-    // weights instead of staging a dark plane with every group of frames
-    const int ent_dk = dark != nullptr;
-    if (ent_dk) {
+    // weights instead of staging a dark plane with every group of frames (given: bound once
+    // by az_set_corrections)
+    const int ent_dk = dark != nullptr || ent_dark_given != nullptr;
+    if (dark && !ent_dark_given) {
         TiledLayout &L = h->tl;
         if (L.ent_dark.bytes < sizeof(float) * (size_t)L.padded_nnz)
             AZ_TRY(L.ent_dark.alloc(sizeof(float) * (size_t)L.padded_nnz));
@@ -1820,6 +1822,7 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
             L.ent_pix.as<int32_t>(), dark, L.padded_nnz, L.ent_dark.as<float>());
         AZ_CUDA(cudaGetLastError());
     }
+    const float *ent_dark = ent_dark_given ? ent_dark_given : h->tl.ent_dark.as<float>();
     // frames per pass as tuned, halved while two stages of that many frame planes do not fit,
     // or while the tile's entries would not fit beside them (down to 4 frames per pass)
     int fpi = h->frames_per_pass;
@@ -1844,9 +1847,10 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
             const int nf = std::min(chunk, n - f0);
             Inst d = make_inst(h, false);
             d.img = static_cast<const char *>(frames) + (size_t)f0 * (size_t)d.npix * 4u;
-            const int rc = frames_v3(h, d.img, nf, dtype, ent_dk ? h->tl.ent_dark.as<float>() : nullptr, 0, s);
+            const int rc = frames_v3(h, d.img, nf, dtype, ent_dk ? ent_dark : nullptr, 0, s);
             if (rc == AZ_EUNSUPPORTED && f0 == 0) break;  // the general kernel below
             AZ_TRY(rc);
+            if (norm) d.norm = const_cast<float *>(norm);
             d.n_frames = nf;
             d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
             AZ_TRY((run_phase2<float, MODE_FRAMES>(d, nullptr, 1, (int64_t)nf * h->nrows, nf, s, &h->prof)));
@@ -1860,7 +1864,8 @@ int batch_frames(az_integrator *h, const void *frames, int n, int dtype, const f
         d.n_frames = nf; d.fpi = fpi; d.n_groups = (nf + fpi - 1) / fpi;
         d.rpw = 32 / fpi;
         d.dark = dark;
-        d.ent_dark = ent_dk ? h->tl.ent_dark.as<float>() : nullptr;
+        d.ent_dark = ent_dk ? ent_dark : nullptr;
+        if (norm) d.norm = const_cast<float *>(norm);
         d.oI = oI; d.oS = oS; d.frame_out0 = frame_out0 + f0;
         d.stage_entries = stage_e;
         d.n_items = h->tl.n_active * d.n_groups;
@@ -2005,6 +2010,47 @@ int forward_batch(az_integrator *h, const void *frames, int n, int dtype, const 
                   float *oN, float *oC, cudaStream_t s) {
     AZ_TRY(batch_norm(h, flat, sa, pol, oN, oC, s));
     return batch_frames(h, frames, n, dtype, dark, oI, oS, 0, s);
+}
+
+// az_set_corrections: the frame-independent work of a batch formed once -- each entry's dark
+// (gathered from `dark`) and N, C per row -- into buffers of their own, which later calls of
+// az_integrate_batch do not touch.  The caller's arrays are not read again.
+int bind_corrections(az_integrator *h, const float *dark, const float *flat, const float *sa,
+                     const float *pol, cudaStream_t s) {
+    TiledLayout &L = h->tl;
+    h->corr_bound = false;
+    h->corr_dark = dark != nullptr;
+    if (dark) {
+        if (h->bound_ent_dark.bytes < sizeof(float) * (size_t)L.padded_nnz)
+            AZ_TRY(h->bound_ent_dark.alloc(sizeof(float) * (size_t)L.padded_nnz));
+        const int64_t blocks = std::min<int64_t>((L.padded_nnz + 255) / 256, (int64_t)num_sms() * 8);
+        ProfScope ps(&h->prof, 4, s);
+        gather_dark_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+            L.ent_pix.as<int32_t>(), dark, L.padded_nnz, h->bound_ent_dark.as<float>());
+        AZ_CUDA(cudaGetLastError());
+    }
+    if (h->bound_norm.bytes < 2 * sizeof(float) * (size_t)h->nrows)
+        AZ_TRY(h->bound_norm.alloc(2 * sizeof(float) * (size_t)h->nrows));
+    float *bN = h->bound_norm.as<float>();
+    AZ_TRY(batch_norm(h, flat, sa, pol, bN, bN + h->nrows, s));
+    h->corr_bound = true;
+    return AZ_OK;
+}
+
+// Frames through the bound corrections: the frames pass with the bound per-entry darks and
+// phase 2 with the bound N.  oN, oC (may be NULL) receive copies of the bound N and C.
+int forward_batch_bound(az_integrator *h, const void *frames, int n, int dtype, float *oI, float *oS,
+                        float *oN, float *oC, cudaStream_t s) {
+    if (!h->corr_bound)
+        return fail(AZ_EINVAL, "az_integrate_batch_bound: no corrections are bound (az_set_corrections), "
+                               "or the tiled layout changed since they were");
+    const float *bN = h->bound_norm.as<float>();
+    const size_t rb = sizeof(float) * (size_t)h->nrows;
+    if (oN) AZ_CUDA(cudaMemcpyAsync(oN, bN, rb, cudaMemcpyDeviceToDevice, s));
+    if (oC) AZ_CUDA(cudaMemcpyAsync(oC, bN + h->nrows, rb, cudaMemcpyDeviceToDevice, s));
+    if (n == 0) return AZ_OK;
+    return batch_frames(h, frames, n, dtype, nullptr, oI, oS, 0, s,
+                        h->corr_dark ? h->bound_ent_dark.as<float>() : nullptr, bN);
 }
 
 // ------------------------------------------------------------------------------------

@@ -77,3 +77,30 @@ def test_selftest_wait_rejects_bad_arguments_on_host():
     assert L.az_selftest_wait(0, 0, C.byref(st), None) == -1
     assert L.az_selftest_wait(0, 3_000_000_000, C.byref(st), None) == -1
     assert st.value == 5
+
+
+def test_csr_import_checks_the_matrix_on_host():
+    """az_csr_import refuses malformed matrices before any device work."""
+    import ctypes as C
+    from paper_1412_6367_gb300 import _lib
+    L = _lib.load()
+
+    def call(indptr, indices, data, ny=2, nx=3, npt=2, lo=0.0, hi=1.0):
+        ip = np.ascontiguousarray(indptr, dtype=np.int32)
+        ix = np.ascontiguousarray(indices, dtype=np.int32)
+        dv = np.ascontiguousarray(data, dtype=np.float64)
+        h = C.c_void_p()
+        return L.az_csr_import(ny, nx, npt, 0, 0, 2, C.c_void_p(ip.ctypes.data), C.c_void_p(ix.ctypes.data),
+                               C.c_void_p(dv.ctypes.data), lo, hi, None, C.byref(h))
+
+    good = ([0, 2, 3], [0, 4, 5], [0.5, 0.5, 1.0])
+    assert call([1, 2, 3], good[1], good[2]) == -1           # indptr[0] != 0
+    assert call([0, 3, 2], good[1], good[2]) == -1           # decreasing indptr
+    assert call(good[0], [0, 6, 5], good[2]) == -1           # pixel outside the detector
+    assert call(good[0], [4, 0, 5], good[2]) == -1           # not ascending within a row
+    assert call(good[0], [0, 0, 5], good[2]) == -1           # duplicate pixel in a row
+    assert call(good[0], good[1], [0.5, np.nan, 1.0]) == -1  # non-finite weight
+    assert call(good[0], good[1], good[2], lo=1.0, hi=1.0) == -1  # empty radial range
+    assert call([0, 0, 0], [0], [1.0]) == -8                 # no entries (AZ_ERANGE)
+    assert call(good[0], good[1], good[2], ny=0) == -2       # bad shape
+    assert b"az_csr_import" in L.az_last_error() or b"csr_build" in L.az_last_error()
