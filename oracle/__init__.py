@@ -26,22 +26,29 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "azint_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_OMP_SRC = os.path.join(_HERE, "azint_omp.c")
+_OMP_PATH = os.path.join(_BUILD, "liboracle_omp.so")
 _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle (gcc, -O2, no FMA contraction) into oracle/_build."""
-    os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+def _compile(src, path, force, extra=()):
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(src):
+        return path
+    tmp = path + ".%d.tmp" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
+           "-shared", *extra, "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, no FMA contraction) and the multi-core CPU baseline
+    (the same, with OpenMP) into oracle/_build."""
+    os.makedirs(_BUILD, exist_ok=True)
+    _compile(_OMP_SRC, _OMP_PATH, force, ("-fopenmp",))
+    return _compile(_SRC, _LIB_PATH, force)
 
 
 class _Geom(ctypes.Structure):
@@ -323,3 +330,59 @@ def integrate_lut(idx, coef, image, dark=None, flat=None, solid_angle=None, pola
 def radial_axis(A: Csr):
     """Bin centres lo + (k + 1/2) delta of the radial axis."""
     return A.lo + (np.arange(A.npt_rad) + 0.5) * A.delta
+
+
+# ---- multi-core CPU baseline (azint_omp.c) ---------------------------------------------
+_omp = None
+
+
+def _load_omp():
+    global _omp
+    with _lock:
+        if _omp is not None:
+            return _omp
+        build()
+        lib = ctypes.CDLL(_OMP_PATH)
+        vp = ctypes.c_void_p
+        lib.omp_threads.restype = ctypes.c_int
+        lib.omp_integrate.argtypes = [ctypes.c_int, ctypes.c_int64] + [vp] * 12
+        lib.omp_integrate.restype = ctypes.c_int
+        _omp = lib
+        return lib
+
+
+@dataclass
+class Csc:
+    """The weight matrix pixel-major (column pointers, row indices, weights)."""
+    colptr: np.ndarray  # int64 [npix + 1]
+    rows: np.ndarray    # int32 [nnz]
+    data: np.ndarray    # float64 [nnz]
+    nrows: int
+    npix: int
+
+
+def csc_of(A: Csr) -> Csc:
+    """The oracle's matrix A regrouped by pixel (scipy.sparse's CSR -> CSC conversion)."""
+    M = A.scipy().tocsc()
+    M.sort_indices()
+    return Csc(np.ascontiguousarray(M.indptr, dtype=np.int64), np.ascontiguousarray(M.indices, dtype=np.int32),
+               np.ascontiguousarray(M.data, dtype=np.float64), A.nrows, A.ny * A.nx)
+
+
+def omp_threads() -> int:
+    return int(_load_omp().omp_threads())
+
+
+def omp_integrate(M: Csc, image_u32, dark=None, flat=None, solid_angle=None, polarization=None):
+    """(I, S, N, C, threads) of the multi-core CPU baseline: the paper's per-thread histograms
+    over the pixels (Sec. 3.4.1) in FP64.  image: uint32 [npix]; corrections float32 or None."""
+    lib = _load_omp()
+    img = np.ascontiguousarray(np.asarray(image_u32).reshape(-1), dtype=np.uint32)
+    cs = [None if a is None else np.ascontiguousarray(np.asarray(a).reshape(-1), dtype=np.float32)
+          for a in (dark, flat, solid_angle, polarization)]
+    I, S, N, C = (np.empty(M.nrows) for _ in range(4))
+    used = lib.omp_integrate(M.nrows, M.npix, _ptr(M.colptr), _ptr(M.rows), _ptr(M.data), _ptr(img),
+                             *[_ptr(a) for a in cs], _ptr(I), _ptr(S), _ptr(N), _ptr(C))
+    if used < 0:
+        raise MemoryError("per-thread histograms")
+    return I, S, N, C, used
