@@ -4,12 +4,17 @@ FP32-compensated forward, frames/s.
 
 A step integrates one batch of --frames frames that are already resident in HBM (the
 batch, 3.2 GB at the default 128 frames, is far larger than the 129 MB L2, so every step
-streams it from DRAM).  Alongside the device-resident number the script reports:
+streams it from DRAM) against the detector's corrections, bound once beforehand like the
+matrix (az_set_corrections).  Alongside the device-resident number the script reports:
+  per_call_corrections  the same batches with the corrections formed again in every call;
   e2e          the same metric through az_integrate_batch_host (pinned host frames, copies
                inside the timed region);
   roofline     achieved HBM GB/s of the dominant kernel (phase-1 frames kernel), timed with
                CUDA events on its stream during the timed region;
-  plain        the one-frame-per-launch FP64 form on the same GPU (the comparator);
+  plain        the one-frame-per-launch FP64 form on the same GPU (the comparator: the faster
+               of the tiled form and the look-up table), with its roofline fraction;
+  parity       relative error per output (I, S, N, C) of frame 0: the FP32 batch and the FP64
+               one-frame form against the oracle, and the two against each other;
   cpu_baseline the oracle (plain C, one thread) on a bounded sample of the same workload.
 
 --impl reference times the oracle alone on the host cores (the reference arm).
@@ -25,6 +30,7 @@ import os
 import re
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -110,6 +116,13 @@ def algorithmic_bytes(nnz, n_unmasked, nrows, frames, dark=True):
     return nnz * 8 + (n_unmasked * 4 if dark else 0) + frames * (n_unmasked * 4 + 16 * nrows)
 
 
+def plain_fp64_bytes(nnz, n_unmasked, nrows):
+    """Algorithmic bytes of one FP64 frame through the matrix: index and FP64 weight per entry,
+    the image and the four correction arrays per pixel, the row pointers and four FP64
+    outputs per row."""
+    return nnz * 12 + n_unmasked * 4 * 5 + 4 * (nrows + 1) + 4 * 8 * nrows
+
+
 def phase1_frames_bytes(nnz, n_unmasked, frames):
     """Algorithmic bytes of one phase-1 frames launch covering `frames` frames."""
     return nnz * 8 + n_unmasked * 4 + frames * n_unmasked * 4
@@ -121,11 +134,11 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % index)
+        fd, self.path = tempfile.mkstemp(prefix="azint_clocks_%d_" % index, suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index),
@@ -138,6 +151,10 @@ class Clocks:
 
     def stop(self):
         if not self.proc:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
             return None
         self.proc.terminate()
         try:
@@ -161,6 +178,11 @@ class Clocks:
                         reasons.add(n)
         except OSError:
             return None
+        finally:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
@@ -244,15 +266,47 @@ def cpu_baseline(w, seconds, check=None):
             break
     parity = None
     if check is not None:
-        frame, got, sa_g, pol_g = check
-        ref = O.integrate(A, frame, dark, flat, sa_g, pol_g)[0]
-        sel = np.abs(ref) > 1e-3 * np.abs(ref).max()
-        parity = {"max_rel_err_I": float(np.max(np.abs(got[sel] - ref[sel]) / np.abs(ref[sel]))),
-                  "nnz_oracle": int(A.nnz)}
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d Pilatus-6M frames integrated one by one by the C oracle (FP64, full "
-                      "split, corrections) in %.1f s; matrix built beforehand" % (n, el),
-            "matrix_build_s": t_build}, parity
+        frame, got32, got64, sa_g, pol_g = check
+        ref = O.integrate(A, frame, dark, flat, sa_g, pol_g)
+        parity = {"nnz_oracle": int(A.nnz), "frame": "frame 0 of the timed batch",
+                  "metric": "max |x - ref| / |ref| over bins with |ref| > 1e-3 max|ref|",
+                  "fp32_batch_vs_oracle": {}, "fp64_one_frame_vs_oracle": {},
+                  "fp32_batch_vs_fp64_one_frame": {}}
+        for k, name in enumerate("ISNC"):
+            parity["fp32_batch_vs_oracle"][name] = rel_max(got32[k], ref[k])
+            parity["fp64_one_frame_vs_oracle"][name] = rel_max(got64[k], ref[k])
+            parity["fp32_batch_vs_fp64_one_frame"][name] = rel_max(got32[k], got64[k])
+        parity["max_rel_err_I"] = parity["fp32_batch_vs_oracle"]["I"]
+    res = {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "%d Pilatus-6M frames integrated one by one by the C oracle (FP64, full "
+                     "split, corrections) in %.1f s; matrix built beforehand" % (n, el),
+           "matrix_build_s": t_build}
+    # the multi-core CPU form of the paper (Sec. 3.4.1: per-thread histograms over the pixels,
+    # OpenMP on every host core), FP64, on the oracle's matrix regrouped by pixel
+    M = O.csc_of(A)
+    ref = O.integrate(A, frames[0], dark, flat, sa, pol)
+    got = O.omp_integrate(M, frames[0], dark, flat, sa, pol)
+    m, t0 = 0, time.perf_counter()
+    while True:
+        _, _, _, _, used = O.omp_integrate(M, frames[m % 4], dark, flat, sa, pol)
+        m += 1
+        el2 = time.perf_counter() - t0
+        if el2 >= seconds * 2 / 3:
+            break
+    res["multicore"] = {
+        "value": m / el2, "unit": UNIT, "cores": int(used), "nproc": os.cpu_count(),
+        "kind": "OpenMP per-thread histograms (oracle/azint_omp.c)",
+        "sample": "%d Pilatus-6M frames one by one, FP64, in %.1f s" % (m, el2),
+        "max_rel_err_vs_oracle": max(rel_max(g_, r_) for g_, r_ in zip(got[:4], ref))}
+    return res, parity
+
+
+def rel_max(got, ref, floor_frac=1e-3):
+    """Largest relative error of `got` over the entries where |ref| > floor_frac max|ref|."""
+    got = np.asarray(got, dtype=np.float64).ravel()
+    ref = np.asarray(ref, dtype=np.float64).ravel()
+    sel = np.abs(ref) > floor_frac * np.abs(ref).max()
+    return float(np.max(np.abs(got[sel] - ref[sel]) / np.abs(ref[sel]))) if sel.any() else 0.0
 
 
 def run_reference(args):
@@ -481,9 +535,29 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
     ig.autotune(16)  # setup, untimed
     ig.integrate_batch(fr[:64])
     ms = _event_ms(torch, lambda: ig.integrate_batch(fr), 16)
+    # beside it, the plain form: one frame per launch, FP64 (the faster of the tiled form and
+    # the look-up table)
+    plain = {}
+    for form in ("tiled", "lut"):
+        call = (lambda k: ig.integrate(fr[k], precision="fp64")) if form == "tiled" else \
+            (lambda k: ig.integrate_lut(fr[k], precision="fp64"))
+        for k in range(3):
+            call(k)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for k in range(32):
+            call(k)
+        b.record()
+        torch.cuda.synchronize()
+        plain[form] = a.elapsed_time(b) / 32
+    best = min(plain, key=plain.get)
     out["stream_4096x2167x2070"] = {"frames_per_s": 256 / (ms / 1e3), "ms_per_4096": 16 * ms,
                                      "autotuned": (ig.info["tile_h"], ig.info["tile_w"],
-                                                   ig.info["frames_per_pass"])}
+                                                   ig.info["frames_per_pass"]),
+                                     "plain_fp64_one_frame_per_launch": {
+                                         "frames_per_s": 1e3 / plain[best], "form": best,
+                                         "ms_per_frame_by_form": plain},
+                                     "speedup_vs_plain": (256 / (ms / 1e3)) / (1e3 / plain[best])}
     del buf, fr, ig
 
     # one Pilatus frame per call through the single-frame path (FP32 compensated)
@@ -528,6 +602,8 @@ def config_dict(w, frames):
     return {"workload": "%s: %dx%d uint32, module-gap mask, q nm^-1, %d bins, full split, "
                         "dark/flat/solid-angle/polarisation" % (w.name, w.ny, w.nx, w.npt_rad),
             "frames_per_step": frames, "precision": "fp32-compensated (Kahan)",
+            "corrections": "bound once per detector (az_set_corrections, setup like the matrix); "
+                           "the per-call form is reported in per_call_corrections",
             "l2": "inputs larger than L2 (frame batch streamed from HBM every step)"}
 
 
@@ -590,15 +666,27 @@ def main():
     out = api.Result(torch.empty((B, ig.nrows), device=dev), torch.empty((B, ig.nrows), device=dev),
                      torch.empty(ig.nrows, device=dev), torch.empty(ig.nrows, device=dev))
 
+    # the detector's corrections are bound once (setup, like the matrix): per-entry darks and
+    # N, C per bin; every step then integrates its frames against them
+    torch.cuda.synchronize()
+    t_bind = time.perf_counter()
+    ig.set_corrections(dark_d, flat_d, sa_d, pol_d)
+    torch.cuda.synchronize()
+    t_bind = time.perf_counter() - t_bind
+
     def step():
-        ig.integrate_batch(frames, dark_d, flat_d, sa_d, pol_d, out=out)
+        ig.integrate_batch_bound(frames, out=out)
 
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
 
-    # the first frame's I, for the parity spot check of the CPU-baseline leg
-    I0 = out.I[0].cpu().numpy().astype(np.float64)
+    # frame 0's four outputs (FP32 batch) and the FP64 one-frame form, for the parity check of
+    # the CPU-baseline leg
+    out32 = [out.I[0], out.sum_signal[0], out.sum_norm, out.count]
+    out32 = [t.double().cpu().numpy() for t in out32]
+    r64 = ig.integrate(frames[0], dark_d, flat_d, sa_d, pol_d, precision="fp64")
+    out64 = [t.cpu().numpy() for t in r64]
 
     # timed region (device-resident inputs)
     clocks = Clocks(local)
@@ -639,26 +727,54 @@ def main():
                 "traffic": traffic_full,
                 "kernel": "frames_kernel<G=%d,U32,dark> (frames pass, %d frames per launch)" % (
                     info["frames_per_pass"], int(per_launch_frames)),
+                "duration_ms_per_launch": tot_ms / max(n_launch, 1),
                 "algorithmic_bytes_per_launch": ab, "peak_source": peak_kind + " hbm_gbs",
                 "kernel_share_of_step": tot_ms / ms if ms else None}
-    step_bytes = algorithmic_bytes(info["nnz"], info["n_unmasked"], ig.nrows, B) + 3 * 4 * info["n_unmasked"]
+    step_bytes = algorithmic_bytes(info["nnz"], info["n_unmasked"], ig.nrows, B)
 
-    # plain comparator: one frame per launch, FP64 accumulation, everything re-read
+    # the same batches with the corrections passed on every call (per-entry darks, N and C
+    # formed again in each call): az_integrate_batch
+    def step_per_call():
+        ig.integrate_batch(frames, dark_d, flat_d, sa_d, pol_d, out=out)
+
+    step_per_call()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step_per_call()
+    b.record()
+    torch.cuda.synchronize()
+    pc_ms = a.elapsed_time(b) / args.steps
+    per_call = {"frames_per_s": B / (pc_ms / 1e3), "ms_per_step": pc_ms, "api": "az_integrate_batch",
+                "bind_ms": t_bind * 1e3}
+
+    # plain comparator: one frame per launch, FP64 accumulation, everything re-read; the
+    # faster of the tiled single-pass form and the look-up table is kept
     plain = None
     if rank == 0:
-        f0 = frames[0]
-        for _ in range(3):
-            ig.integrate(f0, dark_d, flat_d, sa_d, pol_d, precision="fp64")
-        torch.cuda.synchronize()
-        n_plain = 50
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for k in range(n_plain):
-            ig.integrate(frames[k % B], dark_d, flat_d, sa_d, pol_d, precision="fp64")
-        b.record()
-        torch.cuda.synchronize()
-        pms = a.elapsed_time(b) / n_plain
+        forms = {}
+        for form in ("tiled", "lut"):
+            call = (lambda k: ig.integrate(frames[k % B], dark_d, flat_d, sa_d, pol_d, precision="fp64")) \
+                if form == "tiled" else \
+                (lambda k: ig.integrate_lut(frames[k % B], dark_d, flat_d, sa_d, pol_d, precision="fp64"))
+            for k in range(3):
+                call(k)
+            torch.cuda.synchronize()
+            n_plain = 50
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for k in range(n_plain):
+                call(k)
+            b.record()
+            torch.cuda.synchronize()
+            forms[form] = a.elapsed_time(b) / n_plain
+        best = min(forms, key=forms.get)
+        pms = forms[best]
+        pbytes = plain_fp64_bytes(info["nnz"], info["n_unmasked"], ig.nrows)
         plain = {"value": 1e3 / pms, "unit": UNIT, "ms_per_frame": pms, "precision": "fp64",
+                 "form": best, "ms_per_frame_by_form": forms,
+                 "roofline": {"achieved": pbytes / (pms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": pbytes / (pms / 1e3) / 1e9 / peak, "bytes_per_frame": pbytes},
                  "speedup_batched_fp32_vs_plain": value / world / (1e3 / pms)}
 
     # end to end through the host-buffer API (pinned frames, copies inside the timed region)
@@ -676,9 +792,25 @@ def main():
         for _ in range(ksteps):
             ig.integrate_batch_host(host, dark_d, flat_d, sa_d, pol_d, out_I=oI, out_S=oS)
         el = time.perf_counter() - t0
+        # the host link alone: one pinned host -> device copy of the same frames (the ceiling
+        # of any end-to-end rate that uploads them)
+        dbuf = torch.empty(host.numel(), dtype=torch.int32, device=dev)
+        hsrc = host.view(torch.int32).reshape(-1)
+        dbuf.copy_(hsrc, non_blocking=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(3):
+            dbuf.copy_(hsrc, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        link_gbs = 3 * host.numel() * 4 / (a.elapsed_time(b) / 1e3) / 1e9
+        del dbuf
         e2e = {"value": Be * ksteps / el * world, "unit": UNIT,
                "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(2 * oI.numel() * 4),
-               "frames_per_step": Be, "api": "az_integrate_batch_host"}
+               "frames_per_step": Be, "api": "az_integrate_batch_host",
+               "host_link": {"h2d_gbs": link_gbs, "frames_per_s_ceiling": link_gbs * 1e9 / (w.ny * w.nx * 4),
+                             "how": "one pinned cudaMemcpyAsync of the step's frames, CUDA events"}}
 
     others = None
     if rank == 0 and not args.no_other_workloads:
@@ -689,7 +821,7 @@ def main():
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, parity = cpu_baseline(w, args.cpu_seconds,
-                                   check=(base[0], I0, sa_d.cpu().numpy(), pol_d.cpu().numpy()))
+                                   check=(base[0], out32, out64, sa_d.cpu().numpy(), pol_d.cpu().numpy()))
         parity["nnz_gpu"] = int(info["nnz"])
 
     if rank == 0:
@@ -701,6 +833,7 @@ def main():
                 "gpix_per_s": value * w.ny * w.nx / 1e9,
                 "step_algorithmic_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
                 "plain_fp64_one_frame_per_launch": plain, "parity": parity,
+                "per_call_corrections": per_call,
                 "setup": {"csr_build_s": t_build, "nnz": info["nnz"], "n_unmasked": info["n_unmasked"],
                           "segments": info["n_segments"], "tile": [info["tile_h"], info["tile_w"]],
                           "rows_per_warp": info["rows_per_warp"],
