@@ -566,6 +566,12 @@ def other_workloads(torch, dev, ig_pilatus, pilatus_inputs):
         ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32")
     ms = _event_ms(torch, lambda: ig_pilatus.integrate(img, dark, flat, sa, pol, precision="fp32"), 20)
     out["pilatus_single_frame_fp32"] = {"ms_per_frame": ms, "frames_per_s": 1e3 / ms}
+    # the same frame through the corrections bound once (a batch of one)
+    one = img.view(torch.int32).unsqueeze(0).view(torch.uint32)
+    for _ in range(3):
+        ig_pilatus.integrate_batch_bound(one)
+    ms = _event_ms(torch, lambda: ig_pilatus.integrate_batch_bound(one), 20)
+    out["pilatus_single_frame_fp32"]["bound_ms_per_frame"] = ms
 
     # the same frame through the look-up-table layout (Sec. 5.2), FP32 and FP64
     lut = {}
