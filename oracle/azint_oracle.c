@@ -26,7 +26,8 @@
  * library routines (numpy.histogram, scipy rotations, scipy.sparse), brute-force sub-pixel
  * sampling and hand-derived fixtures.  The singular-pixel rule (a pixel whose azimuthal
  * span exceeds 180 degrees after unwrapping, i.e. a pixel containing the beam centre) has
- * no statement in the paper: parity unpinned for those pixels.
+ * no statement in the paper: it is a stated reading (radial bounding box, in 2D times a
+ * uniform azimuth), pinned to that reading by hand-derived fixtures.
  */
 #include <math.h>
 #include <stdint.h>
@@ -389,7 +390,7 @@ static int pixel_1d(const build_ctx *B, int i, int j, entry_list *L)
         double chi[4];
         for (int c = 0; c < 4; ++c) chi[c] = B->chi[k[c]];
         if (unwrap_chi(chi)) {
-            use_bbox = 1; /* singular pixel: reading, parity unpinned */
+            use_bbox = 1; /* singular pixel: the stated reading (radial bounding box) */
         } else {
             /* Sec. 4.2: area of the quad (straight edges in the radial/azimuth plane) inside
              * each bin, in coordinates relative to the first corner. */
@@ -453,7 +454,7 @@ static int pixel_2d(const build_ctx *B, int i, int j, entry_list *L)
     bbox_range(gmin, gmax, 0, nch, &klo, &khi);
 
     if (singular) {
-        /* Reading (parity unpinned): radial bounding box times a uniform azimuth. */
+        /* The stated reading for a singular pixel: radial bounding box times a uniform azimuth. */
         for (int b = blo; b <= bhi && rc == ORC_OK; ++b) {
             double wr = bbox_weight(fmin, fmax, blo, bhi, b);
             for (int kc = 0; kc < nch && rc == ORC_OK; ++kc) rc = push(L, kc * npt + b, wr / nch);

@@ -6,6 +6,7 @@ import numpy as np
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "split_pixels.txt")
 SPLIT_CODES = {"none": 0, "bbox": 1, "full": 2}
+NPT_AZIM = 360  # azimuthal bins of the fixture detector in 2D
 
 
 def load_fixtures():
@@ -24,10 +25,12 @@ def load_fixtures():
             for item in tail.split():
                 key, w = item.split(":")
                 if ndim == 1:
-                    key = (int(key),)
-                else:
-                    key = tuple(int(v) for v in key.split(","))
-                entries[key] = float(Fraction(w))
+                    entries[(int(key),)] = float(Fraction(w))
+                    continue
+                rb, cb = key.split(",")
+                chis = range(NPT_AZIM) if cb == "*" else (int(cb),)
+                for c in chis:
+                    entries[(int(rb), c)] = float(Fraction(w))
             out.append(dict(id=pid, split=SPLIT_CODES[split], ndim=ndim, corners=corners,
                             entries=entries))
     return out
