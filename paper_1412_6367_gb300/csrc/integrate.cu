@@ -855,6 +855,14 @@ __device__ __forceinline__ void fr_stage_planes(const FrArgs &a, const TmaSet &t
     if (lane == 0) mbar_arrive(bar);  // publishes the header and the counter
 }
 
+// Load of a 4-byte word of shared memory at a 32-bit shared-window address (the gathers of
+// the consumers index the staged planes with 32-bit arithmetic).
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
 // Two FP32 values in one 64-bit register, operated on by the packed f32x2 instructions
 // (round to nearest, no flush): each half gives exactly the scalar result.
 typedef unsigned long long f32x2;
@@ -913,7 +921,7 @@ __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, co
     const float *D = W + fg.ent_cap;
     const int nimg = hdr[0], g = hdr[1];
     const bool active = q < nimg;
-    const uint32_t *P = planes + hdr[2 + (active ? q : 0)];
+    const uint32_t P = smem_addr(planes + hdr[2 + (active ? q : 0)]);
     float *out = a.partial + (size_t)(g * G + q) * (size_t)a.nseg;
     while (true) {
         int b = 0;
@@ -934,10 +942,10 @@ __device__ __forceinline__ void fr_consume(const FrArgs &a, const FrGeom &fg, co
             const uint2 l2 = *reinterpret_cast<const uint2 *>(L + qd);
             const float4 w4 = *reinterpret_cast<const float4 *>(W + qd);
             float v[4];
-            v[0] = img_f32<DT>(P[l2.x & 0xffffu]);
-            v[1] = img_f32<DT>(P[l2.x >> 16]);
-            v[2] = img_f32<DT>(P[l2.y & 0xffffu]);
-            v[3] = img_f32<DT>(P[l2.y >> 16]);
+            v[0] = img_f32<DT>(lds_u32(P + ((l2.x & 0xffffu) << 2)));
+            v[1] = img_f32<DT>(lds_u32(P + ((l2.x >> 16) << 2)));
+            v[2] = img_f32<DT>(lds_u32(P + ((l2.y & 0xffffu) << 2)));
+            v[3] = img_f32<DT>(lds_u32(P + ((l2.y >> 16) << 2)));
             if (VM == VM_VAR) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) v[j] = fmaxf(v[j], 0.f);
@@ -991,7 +999,7 @@ __device__ __forceinline__ void fr_consume_split(const FrArgs &a, const FrGeom &
     const float *D = W + fg.ent_cap;
     const int nimg = hdr[0], g = hdr[1];
     const bool active = q < nimg;
-    const uint32_t *P = planes + hdr[2 + (active ? q : 0)];
+    const uint32_t P = smem_addr(planes + hdr[2 + (active ? q : 0)]);
     float *out = a.partial + (size_t)(g * G + q) * (size_t)a.nseg;
     while (true) {
         int b = 0;
@@ -1008,7 +1016,7 @@ __device__ __forceinline__ void fr_consume_split(const FrArgs &a, const FrGeom &
         if (!active) e1 = e0;
         Kahan k{0.f, 0.f};
         for (int e = e0 + j; e < e1; e += 4) {
-            float v = img_f32<DT>(P[L[e]]);
+            float v = img_f32<DT>(lds_u32(P + ((uint32_t)L[e] << 2)));
             float w = W[e];
             if (VM == VM_VAR) {
                 v = fmaxf(v, 0.f);
