@@ -104,3 +104,15 @@ def test_csr_import_checks_the_matrix_on_host():
     assert call([0, 0, 0], [0], [1.0]) == -8                 # no entries (AZ_ERANGE)
     assert call(good[0], good[1], good[2], ny=0) == -2       # bad shape
     assert b"az_csr_import" in L.az_last_error() or b"csr_build" in L.az_last_error()
+
+
+def test_bound_corrections_reject_bad_arguments_on_host():
+    """az_set_corrections and az_integrate_batch_bound refuse a NULL integrator and a
+    negative frame count before touching a device."""
+    from paper_1412_6367_gb300 import _lib
+    L = _lib.load()
+    assert L.az_set_corrections(None, None, None, None, None, None) == -1
+    assert b"az_set_corrections" in L.az_last_error()
+    assert L.az_integrate_batch_bound(None, None, 0, 1, None, None, None, None, None) == -1
+    assert L.az_integrate_batch_bound(None, None, -1, 1, None, None, None, None, None) == -2
+

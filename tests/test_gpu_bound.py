@@ -77,3 +77,25 @@ def test_bound_without_corrections():
     g.set_corrections()
     frames = to_dev(_frames(c, 4, 800))
     assert _same(g.integrate_batch_bound(frames), g.integrate_batch(frames))
+
+
+def test_bound_2d_and_zero_frames():
+    """A 2D (radial x chi) integrator, whose rows have few segments (the per-thread phase 2),
+    and a call with no frames, which only hands back the bound N and C."""
+    w = small_workload(96, 110, npt=40, npt_azim=36, seed=34)
+    c = Case(w)
+    g = c.gpu_from_geometry()
+    corr = c.corrections_dev()
+    g.set_corrections(*corr)
+    fr = _frames(c, 18, 900)
+    frames = to_dev(fr)
+    bound = g.integrate_batch_bound(frames)
+    assert _same(bound, g.integrate_batch(frames, *corr))
+    ref = c.oracle(fr[5])
+    for name, got, r in zip("ISNC", (bound.I[5], bound.sum_signal[5], bound.sum_norm, bound.count), ref):
+        per, norm = rel_err(got.double().cpu().numpy(), r)
+        assert per <= 1e-5 and norm <= 1e-5, (name, per, norm)
+    empty = torch.empty((0, w.ny, w.nx), dtype=torch.int32, device="cuda").view(torch.uint32)
+    none = g.integrate_batch_bound(empty)
+    assert torch.equal(none.sum_norm, bound.sum_norm) and torch.equal(none.count, bound.count)
+    assert g.status() == 0
