@@ -230,7 +230,7 @@ extern "C" int az_integrator_info(const az_integrator *h, az_info *out) {
     const DevBuf *bufs[] = {&h->csr_ptr, &h->csr_idx, &h->csr_w64, &h->csc_ptr, &h->csc_row,
                             &h->csc_w64, &h->csc_w32, &h->tl.tile_seg_ptr, &h->tl.tile_ent_ptr,
                             &h->tl.active_tiles, &h->tl.seg_ent_ptr, &h->tl.seg_slot,
-                            &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_w32, &h->tl.ent_w64,
+                            &h->tl.row_slot_ptr, &h->tl.ent_loc, &h->tl.ent_loc_p, &h->tl.ent_w32, &h->tl.ent_w64,
                             &h->partial, &h->norm, &h->adj, &h->status, &h->host_stage,
                             &h->tl.tile_desc, &h->tl.tile_rec, &h->tl.ent_pix, &h->tl.ent_dark,
                             &h->tl.norm_frames, &h->tl.ent_wnorm, &h->lut32, &h->lut64,

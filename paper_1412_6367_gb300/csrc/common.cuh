@@ -92,6 +92,11 @@ struct TiledLayout {
     DevBuf seg_slot;        // int32 [nseg]        (position of the segment in row order)
     DevBuf row_slot_ptr;    // int32 [nrows + 1]
     DevBuf ent_loc;         // uint16 [padded_nnz] (shared-memory word offset in the tile)
+    // Frame-pair layout of the batched frames kernel (srow_p == 0: none for this tile shape).
+    // Frames F and F + 4 of a stage share a region of pw_p words: F's row-class slots at
+    // sl * ss_p, F + 4's slot_p words (16 mod 32: other banks) later, rows at pitch srow_p.
+    int srow_p = 0, ss_p = 0, slot_p = 0, pw_p = 0;
+    DevBuf ent_loc_p;       // uint16 [padded_nnz] (word offset in the frame-pair layout)
     DevBuf ent_w32;         // float  [padded_nnz]
     DevBuf ent_w64;         // double [padded_nnz]
     DevBuf ent_pix;         // int32  [padded_nnz] (pixel of the entry; -1 for padding)

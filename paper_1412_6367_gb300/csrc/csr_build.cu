@@ -662,6 +662,17 @@ __device__ __forceinline__ int tile_loc(const TileGeom &T, int32_t p) {
     return sl * T.ss + cs + jj * T.srow + lx;
 }
 
+// Offsets of the padded entries in the frame-pair layout (geometry Tp): the same formula at
+// the pair layout's row pitch and slot stride; padding entries read the zero band at 4 ss.
+__global__ void pair_loc_kernel(TileGeom Tp, const int32_t *__restrict__ pix, int64_t n,
+                                uint16_t *__restrict__ loc) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = pix[e];
+        loc[e] = (uint16_t)(p >= 0 ? tile_loc(Tp, p) : 4 * Tp.ss);
+    }
+}
+
 __global__ void tile_keys_kernel(TileGeom T, const int32_t *__restrict__ idx, int64_t n,
                                  uint32_t *__restrict__ key) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
@@ -1191,6 +1202,32 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     A.pix = L.ent_pix.as<int32_t>(); A.n = nnz;
     AZ_TRY(launch_gs(tiled_fill_kernel, nnz, s, A));
 
+    // Frame-pair layout: a 3D copy of one row class of frames F and F + 4 writes the two
+    // frames' boxes (th / 4 rows of srow_p words each) back to back, so F + 4 sits slot_p =
+    // (th / 4) srow_p words after F.  slot_p = 16 mod 32 puts the two frames on different
+    // banks; slots of 2 slot_p words keep F's slots 128-byte aligned; boxes are at most 256
+    // words wide.  Tile shapes without such a pitch use the plain layout only.
+    int srow_p = 0, ss_p = 0, slot_p = 0, pw_p = 0;
+    for (int sr = T.srow; sr <= 256 && !srow_p; sr += 4)
+        if (((th / 4) * sr) % 32 == 16) srow_p = sr;
+    if (srow_p) {
+        slot_p = (th / 4) * srow_p;
+        ss_p = 2 * slot_p;
+        pw_p = (4 * ss_p + slot_p + 32 + 31) & ~31;
+        if (pw_p > 65535) srow_p = 0;
+    }
+    L.ent_loc_p.release();
+    if (srow_p) {
+        TileGeom Tp = T;
+        Tp.srow = srow_p;
+        Tp.ss = ss_p;
+        AZ_TRY(L.ent_loc_p.alloc(sizeof(uint16_t) * (size_t)padded));
+        AZ_TRY(launch_gs(pair_loc_kernel, padded, s, Tp, L.ent_pix.as<int32_t>(), (int64_t)padded,
+                         L.ent_loc_p.as<uint16_t>()));
+    } else {
+        ss_p = slot_p = pw_p = 0;
+    }
+
     // slots: segments in row order (stable sort of segment ids by row)
     DevBuf skey, sperm, rcnt;
     AZ_TRY(skey.alloc(sizeof(uint32_t) * nseg));
@@ -1268,6 +1305,7 @@ int build_tiled_layout(az_integrator *h, int th, int tw, cudaStream_t s) {
     const int32_t max_rec = maxes[2];
 
     L.th = th; L.tw = tw; L.srow = T.srow; L.ss = T.ss; L.ntx = T.ntx; L.nty = nty; L.ntiles = ntiles;
+    L.srow_p = srow_p; L.ss_p = ss_p; L.slot_p = slot_p; L.pw_p = pw_p;
     L.n_active = n_active; L.nseg = nseg; L.padded_nnz = padded;
     L.max_tile_entries = maxes[0]; L.max_tile_segments = maxes[1];
     L.max_rec_words = max_rec;

@@ -140,21 +140,27 @@ __device__ __forceinline__ TileDesc load_desc(const Inst &d, int64_t local) {
 constexpr uint32_t kZeroBand = 32;
 __host__ __device__ __forceinline__ uint32_t plane_stride(int ss) { return 4u * (uint32_t)ss + kZeroBand; }
 
-// Zero the band after every plane of every stage (never written by the copies).
+// Zero words band_from .. pw - 1 of every plane of every stage (never written by the copies):
+// the band after a plane, or in the frame-pair layout the tail of a region that holds both
+// frames' bands.
 __device__ __forceinline__ void zero_bands(unsigned char *first_plane, uint32_t stage_bytes, int nstages,
-                                           int planes, uint32_t pw) {
-    const int per_stage = planes * (int)kZeroBand;
+                                           int planes, uint32_t pw, uint32_t band_from) {
+    const int band = (int)(pw - band_from);
+    const int per_stage = planes * band;
     for (int i = threadIdx.x; i < nstages * per_stage; i += blockDim.x) {
         const int st = i / per_stage, r = i - st * per_stage;
-        const int pl = r / (int)kZeroBand, w = r - pl * (int)kZeroBand;
-        reinterpret_cast<uint32_t *>(first_plane + (size_t)st * stage_bytes)[(size_t)pl * pw + pw - kZeroBand + w] = 0u;
+        const int pl = r / band, w = r - pl * band;
+        reinterpret_cast<uint32_t *>(first_plane + (size_t)st * stage_bytes)[(size_t)pl * pw + band_from + w] = 0u;
     }
 }
 
 // Four 2D tensor maps per staged array, one per tile-row class (rows of equal index mod 4,
 // 16 * nx bytes apart).  Index: 0 image, 1 dark, 2 flat, 3 solid angle, 4 polarisation.
+// pair: the image's four class maps in three dimensions (x, class row, period of four
+// frames) for the frame-pair layout of the frames kernel.
 struct TmaSet {
     CUtensorMap m[5][4];
+    CUtensorMap pair[4];
 };
 
 // Stage layout: [header 256 B][tile record][planes][entry locs][entry weights].
@@ -742,6 +748,8 @@ struct FrArgs {
     int nseg, ny, nx, th, tw, srow, ss, ntx;
     int *status;
     int var;                              // sum w^2 max(img, 0) instead of w img
+    int pair;                             // frame-pair layout (8 frames per stage, whole stages)
+    int slot;                             // its offset of frame F + 4 from frame F (words)
 };
 
 struct FrGeom {
@@ -749,8 +757,9 @@ struct FrGeom {
     uint32_t ent_cap;       // entry capacity (multiple of 8)
     uint32_t ebuf_bytes;    // one entry buffer (multiple of 128)
     int nebufs;             // entry buffers in the ring (2 .. kFrMaxEbufs)
-    uint32_t plane_words;   // words per plane
-    uint32_t pstage_bytes;  // one plane stage: G planes
+    uint32_t plane_words;   // words per plane (frame-pair layout: per region of two frames)
+    uint32_t band_from;     // first word of a plane's zero band
+    uint32_t pstage_bytes;  // one plane stage: G planes (G / 2 regions)
     int nstages;            // plane stages
     int dk;                 // entries carry a dark
 };
@@ -778,6 +787,63 @@ __device__ __forceinline__ void fr_stage_entries(const FrArgs &a, const FrGeom &
     }
 }
 
+// The producer warp in the frame-pair layout (a whole stage of 8 frames): frames q and q + 4
+// (q < 4) share region q of the stage, and one 3D tensor copy per (q, row class) moves that
+// class of both frames -- periods m and m + 1 of the pair maps, m = (f0 + q) / 4 -- so a
+// stage takes 16 copies.  Frame q's box starts 4 s_q words early as in fr_stage_planes (s_q =
+// (q / P) mod 4 for the phase period P of the first four frames); frame q + 4, whose rows are
+// 4 ny rows later, has frame q's word phase and shift, and its plane is a.slot words after
+// frame q's.  Lane 0 then publishes the stage header and resets the stage's claim counter.
+__device__ __forceinline__ void fr_stage_pairs(const FrArgs &a, const TmaSet &tm, const TileDesc &td, int g,
+                                               uint32_t *planes, int *hdr, const FrGeom &fg, uint64_t *bar,
+                                               int *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int ti = td.t / a.ntx, tj = td.t - ti * a.ntx;
+    const int r0 = ti * a.th, c0 = tj * a.tw;
+    const int f0 = g * 8;
+    const int nu = a.nx & 3;
+    const int rows4 = a.th >> 2;
+    const uint32_t pw = fg.plane_words;
+    const int beta = (int)((reinterpret_cast<uintptr_t>(a.img) >> 2) & 3u);
+    const int c = (nu * (a.ny & 3)) & 3;
+    const int lp = c == 0 ? 0 : (c == 2 ? 1 : 2);  // log2 of the phase period P
+    const int q = (lane >> 2) & 3, k = lane & 3;     // lanes 0..15: (frame q, class k)
+    const int phi_row = (int)(((int64_t)(f0 + q) * a.ny + r0) & 3);
+    const int phi = (beta + nu * phi_row) & 3;
+    const int sq = (q >> lp) & 3;
+    fence_proxy_async_smem();
+    if (lane == 0)
+        asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                     "r"((uint32_t)(16 * a.srow * rows4 * 2 * 4))
+                     : "memory");
+    __syncwarp();
+    if (lane < 16) {
+        const int sl = (k - phi_row) & 3;
+        const int offk = (beta + k * nu) & 3;
+        const int flag = (((nu * sl) & 3) + phi - offk) >> 2;
+        const int x = c0 - 4 * (flag + sq);
+        const int y = (q * a.ny + r0 + sl - k) >> 2;  // class row within the period (exact)
+        const int m = (f0 + q) >> 2;
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(planes + (size_t)q * pw + (size_t)sl * a.ss)),
+            "l"(reinterpret_cast<uint64_t>(&tm.pair[k])), "r"(x), "r"(y), "r"(m), "r"(smem_addr(bar))
+            : "memory");
+    }
+    if (lane < 8) {
+        const int qa = lane & 3;
+        const int pha = (beta + nu * (int)(((int64_t)(f0 + qa) * a.ny + r0) & 3)) & 3;
+        hdr[2 + lane] = (int)(qa * pw) + (lane >> 2) * a.slot + pha + 4 * ((qa >> lp) & 3);
+    }
+    if (lane == 0) {
+        hdr[0] = 8;
+        hdr[1] = g;
+        *ctr = 0;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);  // publishes the header and the counter
+}
+
 // The producer warp: frames f0 .. f0 + nimg - 1 of the tile into plane stage `planes`, one
 // tensor copy per (frame, row class), as in produce(); G <= 16, so a lane has at most two
 // copies.  Frame q's box starts 4 * s_q words early, s_q = (number of earlier frames of the
@@ -789,6 +855,12 @@ __device__ __forceinline__ void fr_stage_planes(const FrArgs &a, const TmaSet &t
                                                 int g, uint32_t *planes, int *hdr, const FrGeom &fg,
                                                 uint64_t *bar, int *ctr) {
     static_assert(G >= 1 && G <= 16, "a plane stage holds at most 16 frames");
+    if constexpr (G == 8) {
+        if (a.pair) {
+            fr_stage_pairs(a, tm, td, g, planes, hdr, fg, bar, ctr);
+            return;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int ti = td.t / a.ntx, tj = td.t - ti * a.ntx;
     const int r0 = ti * a.th, c0 = tj * a.tw;
@@ -797,7 +869,7 @@ __device__ __forceinline__ void fr_stage_planes(const FrArgs &a, const TmaSet &t
     const int nu = a.nx & 3;
     const int rows4 = a.th >> 2;
     const int64_t rows_total = (int64_t)a.n_frames * a.ny;
-    const uint32_t pw = plane_stride(a.ss);
+    const uint32_t pw = fg.plane_words;
     const int beta = (int)((reinterpret_cast<uintptr_t>(a.img) >> 2) & 3u);
     // lane q < nimg: word phase of frame q's tile rows and its shift (earlier frames of the
     // group with the same phase, mod 4)
@@ -1068,7 +1140,8 @@ frames_kernel(const __grid_constant__ FrArgs a, FrGeom fg, const __grid_constant
         *abort_flag = 0;
         fence_barrier_init();
     }
-    zero_bands(pst, fg.pstage_bytes, S, (int)(fg.pstage_bytes / (fg.plane_words * 4u)), fg.plane_words);
+    zero_bands(pst, fg.pstage_bytes, S, (int)(fg.pstage_bytes / (fg.plane_words * 4u)), fg.plane_words,
+               fg.band_from);
     __syncthreads();
     if (warp == 0) {
         int k = 0, issued = 0;  // items seen, items whose entries were issued
@@ -1493,14 +1566,46 @@ uint32_t rec_words_of(const az_integrator *h) { return (uint32_t)h->tl.max_rec_w
 // ---- frames kernel with tile-resident entries -----------------------------------------
 constexpr uint32_t kFrFixedBytes = 128 + 384;  // alignment slack; barriers, counters, flag
 
-// Sizes for G frames per plane stage; false unless two entry buffers and two plane stages fit.
-bool fr_geom(const az_integrator *h, int G, int dk, int n_groups, FrGeom &fg) {
+// The image's row-class maps for the frame-pair layout, in three dimensions: x, the ny class
+// rows of a period of four frames (class k holds rows k, k + 4, ... of the stacked frames, so
+// a period is 4 ny rows = ny class rows), and the period (16 npix bytes, a multiple of 16).
+// Class k of frames F and F + 4 are the same class rows of consecutive periods, so a box of
+// depth 2 copies both.  Only the nf / 4 whole periods of the nf frames are mapped.
+int encode_pair_maps(const void *img, int nf, int ny, int nx, int box_w, int box_h, CUtensorMap out[4]) {
+    AZ_TRY(get_encoder());
+    const uintptr_t base = reinterpret_cast<uintptr_t>(img);
+    const int beta = (int)((base >> 2) & 3u), nu = nx & 3;
+    for (int k = 0; k < 4; ++k) {
+        const int offk = (beta + k * nu) & 3;
+        void *basek = reinterpret_cast<void *>(base + 4u * (uintptr_t)k * (uintptr_t)nx - 4u * (uintptr_t)offk);
+        cuuint64_t dims[3] = {(cuuint64_t)(nx + offk), (cuuint64_t)ny, (cuuint64_t)(nf / 4)};
+        cuuint64_t strides[2] = {(cuuint64_t)16 * (cuuint64_t)nx, (cuuint64_t)16 * (cuuint64_t)nx * (cuuint64_t)ny};
+        cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 2};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUresult r = g_encode(&out[k], CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, basek, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(AZ_ECUDA, "cuTensorMapEncodeTiled (pairs) failed (%d)", (int)r);
+    }
+    return AZ_OK;
+}
+
+// Sizes for G frames per plane stage (pair: the frame-pair layout, G / 2 regions of two
+// frames); false unless two entry buffers and two plane stages fit.
+bool fr_geom(const az_integrator *h, int G, int dk, int n_groups, FrGeom &fg, bool pair = false) {
     fg.rec_cap = (rec_words_of(h) * 4u + 127u) & ~127u;
     fg.ent_cap = ((uint32_t)h->tl.max_tile_entries + 7u) & ~7u;
     fg.dk = dk;
     fg.ebuf_bytes = (fg.rec_cap + fg.ent_cap * (dk ? 10u : 6u) + 127u) & ~127u;
-    fg.plane_words = plane_words_of(h);
-    fg.pstage_bytes = (uint32_t)G * fg.plane_words * 4u;
+    if (pair) {
+        fg.plane_words = (uint32_t)h->tl.pw_p;
+        fg.band_from = 4u * (uint32_t)h->tl.ss_p;
+        fg.pstage_bytes = (uint32_t)(G / 2) * fg.plane_words * 4u;
+    } else {
+        fg.plane_words = plane_words_of(h);
+        fg.band_from = fg.plane_words - kZeroBand;
+        fg.pstage_bytes = (uint32_t)G * fg.plane_words * 4u;
+    }
     // two entry buffers and as many plane stages as fit; then, when a work item has few
     // frame groups (the entries dominate its copies), more entry buffers in what is left
     const int64_t per = (int64_t)fg.pstage_bytes + kFrStageHeader;
@@ -1562,16 +1667,19 @@ int fr_launch_dt(int dtype, const FrArgs &a, const FrGeom &fg, const TmaSet &tm,
     }
 }
 
-// Frames kernel over `nf` frames starting at `img` (nf <= the partial buffer's frames):
-// per-segment partials [nf][nseg] in h->partial.  Returns AZ_EUNSUPPORTED (without error
-// text) when the TMA engine or the shared memory it needs is not available.
+// Frames kernel over `nf` frames starting at `img` (nf <= the partial buffer's frames from
+// frame0 on): per-segment partials [nf][nseg] in h->partial from frame frame0.  With 8 frames
+// per stage, whole stages go through the frame-pair layout when the tile shape has one and
+// its stages fit; the frames of a last partial stage then go through the plain layout in a
+// second launch (a frame's sums do not depend on the layout it is read through: the entry
+// order is the same).  Returns AZ_EUNSUPPORTED (without error text) when the TMA engine or
+// the shared memory it needs is not available.
 int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float *ent_dark,
-              int prof_kind, cudaStream_t s, bool var = false, const float *ent_weights = nullptr) {
+              int prof_kind, cudaStream_t s, bool var = false, const float *ent_weights = nullptr,
+              int frame0 = 0, bool allow_pair = true) {
     if (engine_for(h) != AZ_COPY_TMA) return AZ_EUNSUPPORTED;
     int G = h->frames_per_pass >= 16 ? 16 : (h->frames_per_pass >= 8 ? 8 : 4);
     FrGeom fg;
-    // one or two frames of float values without a dark (the norm pass): one lane per
-    // segment and frame, 32 / nf segments per warp
     // one frame (any image type, with or without a dark), or two frames of float values
     // without a dark (the norm pass): one lane per segment and frame
     const bool small = nf == 1 || (nf == 2 && dtype == AZ_DTYPE_F32 && ent_dark == nullptr && !var);
@@ -1584,19 +1692,37 @@ int frames_v3(az_integrator *h, const void *img, int nf, int dtype, const float 
     }
     if (!fits) return AZ_EUNSUPPORTED;
     const TiledLayout &L = h->tl;
+    const int nf8 = nf & ~7;
+    FrGeom fp;
+    const bool pair = allow_pair && G == 8 && !small && L.srow_p > 0 && nf8 > 0 &&
+                      fr_geom(h, 8, ent_dark != nullptr, nf8 / 8, fp, true);
+    if (pair) fg = fp;
+    const int nrun = pair ? nf8 : nf;
     FrArgs a{};
     a.img = static_cast<const char *>(img);
-    a.n_frames = nf; a.n_groups = (nf + G - 1) / G; a.n_tiles = L.n_active;
+    a.n_frames = nrun; a.n_groups = (nrun + G - 1) / G; a.n_tiles = L.n_active;
     a.tile_desc = L.tile_desc.as<int32_t>(); a.tile_rec = L.tile_rec.as<int32_t>();
-    a.ent_loc = L.ent_loc.as<uint16_t>();
+    a.ent_loc = pair ? L.ent_loc_p.as<uint16_t>() : L.ent_loc.as<uint16_t>();
     a.ent_w = ent_weights ? ent_weights : L.ent_w32.as<float>();
     a.ent_dark = ent_dark;
     a.var = var ? 1 : 0;
-    a.partial = h->partial.as<float>();
-    a.nseg = L.nseg; a.ny = h->ny; a.nx = h->nx; a.th = L.th; a.tw = L.tw; a.srow = L.srow;
-    a.ss = L.ss; a.ntx = L.ntx;
+    a.partial = h->partial.as<float>() + (size_t)frame0 * (size_t)L.nseg;
+    a.nseg = L.nseg; a.ny = h->ny; a.nx = h->nx; a.th = L.th; a.tw = L.tw;
+    a.srow = pair ? L.srow_p : L.srow;
+    a.ss = pair ? L.ss_p : L.ss;
+    a.ntx = L.ntx;
+    a.pair = pair ? 1 : 0;
+    a.slot = L.slot_p;
     a.status = h->status.as<int>();
     TmaSet tm;
+    if (pair) {
+        memset(&tm, 0, sizeof(tm));
+        AZ_TRY(encode_pair_maps(img, nrun, h->ny, h->nx, L.srow_p, L.th / 4, tm.pair));
+        AZ_TRY(fr_launch_dt<8>(dtype, a, fg, tm, s, &h->prof, prof_kind));
+        if (nrun == nf) return AZ_OK;
+        return frames_v3(h, static_cast<const char *>(img) + (size_t)nrun * (size_t)h->ny * (size_t)h->nx * 4u,
+                         nf - nrun, dtype, ent_dark, prof_kind, s, var, ent_weights, frame0 + nrun, false);
+    }
     AZ_TRY(make_maps(h, AZ_COPY_TMA, img, (int64_t)nf * h->ny, nullptr, nullptr, nullptr, nullptr, tm));
     if (small)
         return G == 1 ? fr_launch_dt<1>(dtype, a, fg, tm, s, &h->prof, prof_kind)
