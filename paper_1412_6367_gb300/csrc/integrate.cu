@@ -5,7 +5,7 @@
 //     a heavy one) for every frame of the launch.  One producer warp copies the item's
 //     record and entries (location, weight, per-entry dark) once into a ring of entry
 //     buffers and streams the tile's pixels, G frames at a time, into a ring of plane stages
-//     (bulk and tensor TMA, mbarrier-tracked, every wait bounded); 16 consumer warps give
+//     (bulk and tensor TMA, mbarrier-tracked, every wait bounded); 15 consumer warps give
 //     lanes (segment, frame) pairs and write one partial sum per (segment, frame).  It serves
 //     batches, the frame-independent sums N and C, the propagated variance, the per-pixel-
 //     corrected form and single FP32 frames (after single_planes_kernel forms the corrected
@@ -726,10 +726,12 @@ phase1_kernel(const __grid_constant__ Inst single, const Inst *__restrict__ mult
 // tile for every frame of the launch: the tile's record and entries (location, weight,
 // dark) are copied once into one of two entry buffers and stay there while the tile's
 // pixels stream through a ring of plane stages, G frames per stage.  One producer warp
-// issues every copy (bulk and tensor TMA); 16 consumer warps reduce.  The consumer
+// issues every copy (bulk and tensor TMA); 15 consumer warps reduce (16 warps in all, four
+// per scheduler: with 16 consumers the 64-frame Pilatus pass took 2.5% longer, with 20 or
+// 24 longer still).  The consumer
 // arithmetic is exactly that of the frames mode of phase1_kernel: the same entry order,
 // accumulator assignment and merge, so results do not depend on the kernel that made them.
-constexpr int kFrConsumers = 16;
+constexpr int kFrConsumers = 15;
 constexpr int kFrThreads = 32 * (1 + kFrConsumers);
 constexpr int kFrMaxStages = 8;
 constexpr int kFrMaxEbufs = 6;
@@ -798,9 +800,21 @@ __device__ __forceinline__ void fr_stage_pairs(const FrArgs &a, const TmaSet &tm
                                                uint32_t *planes, int *hdr, const FrGeom &fg, uint64_t *bar,
                                                int *ctr) {
     const int lane = threadIdx.x & 31;
+    const int f0 = g * 8;
+    if (a.n_frames - f0 < 8) {
+        // a partial stage (the host launches whole stages only): no frames, an error status
+        if (lane == 0) {
+            atomicExch(a.status, AZ_EINVAL);
+            hdr[0] = 0;
+            hdr[1] = g;
+            *ctr = 0;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar);
+        return;
+    }
     const int ti = td.t / a.ntx, tj = td.t - ti * a.ntx;
     const int r0 = ti * a.th, c0 = tj * a.tw;
-    const int f0 = g * 8;
     const int nu = a.nx & 3;
     const int rows4 = a.th >> 2;
     const uint32_t pw = fg.plane_words;
