@@ -64,6 +64,10 @@ def parse(argv=None):
     ap.add_argument("--only-single", action="store_true",
                     help="run only one Pilatus-6M frame per call (FP32, corrections; 3 warm-up "
                          "+ --steps calls) and print its time")
+    ap.add_argument("--only-stream", action="store_true",
+                    help="run only the 2167 x 2070 stream (--frames frames per call, 16 x 96 "
+                         "tiles and 8 frames per pass, no autotuning; 1 warm-up + --steps calls) "
+                         "and print its rate")
     ap.add_argument("--instances", type=int, default=64,
                     help="instances of the many-instance launch with --only-batching")
     return ap.parse_args(argv)
@@ -438,6 +442,29 @@ def cake_workload(torch, dev, gen, reps=5):
     return res
 
 
+def stream_only(torch, dev, gen, reps, nframes):
+    """The 2167 x 2070 / 2000-bin stream alone at a fixed tuning (16 x 96 tiles, 8 frames per
+    pass: the frame-pair staging), nframes-frame device calls: frames/s and the frames pass."""
+    from paper_1412_6367_gb300 import api, synth
+    w = synth.stream_workload()
+    g = api.Geometry(*w.geometry.astuple())
+    ig = api.Integrator.build(g, (w.ny, w.nx), w.npt_rad, 0, "q_nm^-1", "full", device=dev)
+    fr = torch.randint(0, 4000, (nframes, w.ny, w.nx), generator=gen, device=dev, dtype=torch.int32)
+    fr = fr.view(torch.uint32)
+    ig.set_tuning(16, 96, 0, 8)
+    ig.integrate_batch(fr)
+    ig.profile_read()
+    ig.profile_enable(True)
+    ms = _event_ms(torch, lambda: ig.integrate_batch(fr), reps)
+    ig.profile_enable(False)
+    n, k = ig.profile_read()["phase1_frames"]
+    res = {"frames_per_s": nframes / (ms / 1e3), "frames_per_call": nframes, "tuning": [16, 96, 8],
+           "nnz": ig.info["nnz"],
+           "frames_pass_ms_per_64": k / max(n, 1)}
+    del fr, ig
+    return res
+
+
 def single_frame_workload(torch, dev, reps=20):
     """One Pilatus-6M uint32 frame per call, FP32 compensated, with dark, flat, solid angle
     and polarisation: ms per frame."""
@@ -630,6 +657,11 @@ def main():
         gen = torch.Generator(device=dev)
         gen.manual_seed(7)
         print(json.dumps({"cake_2048x2048_500x360": cake_workload(torch, dev, gen, args.steps)}))
+        return
+    if args.only_stream:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        print(json.dumps({"stream_2167x2070": stream_only(torch, dev, gen, args.steps, args.frames)}))
         return
     if args.only_single:
         print(json.dumps({"pilatus_single_frame_fp32": single_frame_workload(torch, dev, args.steps)}))
