@@ -8,7 +8,7 @@ streams it from DRAM) against the detector's corrections, bound once beforehand 
 matrix (az_set_corrections).  Alongside the device-resident number the script reports:
   per_call_corrections  the same batches with the corrections formed again in every call;
   e2e          the same metric through az_integrate_batch_host (pinned host frames, copies
-               inside the timed region);
+               inside the timed region; --e2e-frames frames per call, by default the step's);
   roofline     achieved HBM GB/s of the dominant kernel (phase-1 frames kernel), timed with
                CUDA events on its stream during the timed region;
   plain        the one-frame-per-launch FP64 form on the same GPU (the comparator: the faster
@@ -49,7 +49,8 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=128, help="frames per step (per GPU)")
-    ap.add_argument("--e2e-frames", type=int, default=32)
+    ap.add_argument("--e2e-frames", type=int, default=128,
+                    help="frames per end-to-end call (at most --frames; default: the step's)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
