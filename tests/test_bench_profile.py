@@ -43,3 +43,19 @@ def test_other_source_gives_no_traffic(tmp_path, monkeypatch):
     assert b.ncu_traffic() is None
     monkeypatch.setattr(b, "frames_kernel_sha", lambda: "0" * 64)
     assert b.ncu_traffic() == (123.0, 64)
+
+
+def test_profile_commands_run_committed_options():
+    """Every bench.py command written in a profile summary parses with the benchmark's own
+    options (the summaries name committed files and flags only)."""
+    b = _bench()
+    found = 0
+    for name in sorted(os.listdir(os.path.join(ROOT, "profiles"))):
+        text = open(os.path.join(ROOT, "profiles", name)).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            if "python bench.py" not in line:
+                continue
+            args = line.split("python bench.py", 1)[1].split()
+            b.parse(args)  # SystemExit on an unknown option
+            found += 1
+    assert found >= 4
